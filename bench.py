@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Throughput of the fused EM-Step on one GB300: particle-steps per second.
+
+Workload (per GPU): the 16-edge Langevin star -- lengths U[0.5, 2],
+quadratic potentials V_e = a_e (x - c_e)^2 with a_e ~ U[0.5, 4], c_e ~ U[0,
+L_e], sigma = sqrt(2), equal jump weights, reflecting leaves -- with
+N = 2^24 particles, dt = 1e-3, M = 16 splits per step at most, FP32-mixed,
+and a fused 32-bin-per-edge snapshot histogram.  One benchmark step is one
+mg_simulate call of 10^4 EM-Steps over all particles (one kernel launch) on
+device-resident state.  The state (N x 20 bytes = 335 MB) is larger than L2,
+so no explicit flush is needed between steps.
+
+Printed: one JSON line (rank 0).  ``value`` is device-timed (CUDA events on
+the launch stream); ``e2e`` times the same work through the C ABI with host
+buffers: positions uploaded from pinned host memory (mg_particles_reset),
+mg_simulate, the histogram and the counters read back to the host.
+``--impl reference`` times the plain CPU oracle on the host cores instead.
+Under torchrun each rank simulates its own N particles (ids rank*N ..), so
+the scaling is weak; there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2512_02175_gb300 import workloads as W  # noqa: E402
+
+DT, EM_STEPS, M, BINS, SEED = 1e-3, 10_000, 16, 32, 0
+# Algorithmic thread-instructions of one particle-step on the fast path (the
+# floor without vertex hits): Philox-4x32-10 per 4 steps = 10 rounds x (2 wide
+# multiplies + 2 three-input XORs) / 4 = 10; Box-Muller per normal = 7; EM
+# update 2 FMA, interior test 2 compares + 1 branch = 5; loop control 1.
+I_ALG = 23
+METRIC = "particle-steps/sec"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--em-steps", type=int, default=EM_STEPS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16_384)
+    return ap.parse_args()
+
+
+def config(args, world):
+    return {"workload": "star16_langevin", "graph": "star, 16 edges, L~U[0.5,2], quadratic "
+            "potentials, sigma=sqrt(2), equal b, reflecting leaves",
+            "n_particles_per_gpu": args.n, "global_particles": args.n * world,
+            "dt": DT, "em_steps_per_step": args.em_steps, "M": M, "hist_bins_per_edge": BINS,
+            "precision": "fp32-mixed" if args.precision == "fp32" else "fp64",
+            "parallelism": f"particle shards x{world}", "l2": "state 20 B/particle > L2"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+               "200"]
+        if gpu_id is not None:
+            cmd += ["-i", str(gpu_id)]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 6]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ cpu oracle
+
+def _oracle_chunk(args):
+    desc, edge, x, pid, steps = args
+    from oracle import oracle as O
+    g = O.Graph.from_desc(desc)
+    st = O.State(edge, x, pid)
+    cnt = O.Counters(g)
+    O.simulate(g, st, cnt, seed=SEED, instance=0, t0=0, dt=DT, steps=steps, M=M)
+    return int(cnt.particle_steps[0])
+
+
+def cpu_oracle(desc, e0, x0, sample, steps, pool, cores):
+    """Times the plain oracle on `sample` particles x `steps` EM-Steps."""
+    d = {k: desc[k] for k in ("n_vertices", "src", "dst", "length", "c0", "c1", "sigma",
+                              "w_init", "w_term")}
+    b = np.linspace(0, sample, cores + 1).astype(int)
+    jobs = [(d, e0[i:j], x0[i:j], np.arange(i, j, dtype=np.uint32), steps)
+            for i, j in zip(b[:-1], b[1:]) if j > i]
+    t = time.perf_counter()
+    ps = sum(pool.map(_oracle_chunk, jobs))
+    return ps, time.perf_counter() - t
+
+
+def make_pool():
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    desc = W.star_langevin(16)
+    e0, x0 = W.uniform_on_edges(desc, args.cpu_sample, 11)
+    pool, cores = make_pool()
+    sample = args.cpu_sample
+    for _ in range(args.warmup):
+        cpu_oracle(desc, e0, x0, sample, args.em_steps, pool, cores)
+    total_ps, total_t = 0, 0.0
+    for _ in range(args.steps):
+        ps, t = cpu_oracle(desc, e0, x0, sample, args.em_steps, pool, cores)
+        total_ps += ps
+        total_t += t
+    pool.close()
+    v = total_ps / total_t
+    desc_sample = (f"{sample} particles x {args.em_steps} EM-Steps per step of the "
+                   f"star16_langevin workload (pids 0..{sample - 1}), FP64 oracle, "
+                   f"{cores} processes")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args, 1),
+        "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": cores,
+                         "kind": "oracle", "sample": desc_sample},
+        "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# --------------------------------------------------------------- our path
+
+def _traffic(kernel_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "em_step_star16_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sha256") != kernel_hash:
+        return None
+    return rec.get("dram_bytes_per_launch_full_size")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_02175_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    desc = W.star_langevin(16)
+    n = args.n
+    # the rank's shard: particles rank*n .. rank*n + n - 1 of the global workload
+    e0, x0 = W.uniform_on_edges(desc, n, 11 + rank)
+    pool = cores = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, cores = make_pool()  # spawn, before the first CUDA call
+        ce, cx = W.uniform_on_edges(desc, args.cpu_sample, 11)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    B.use_torch_allocator()
+    prec = B.MG_FP32_MIXED if args.precision == "fp32" else B.MG_FP64
+    stream = torch.cuda.Stream()
+    g = B.Graph(desc)
+    p = B.Particles(g, e0, x0, pid_base=rank * n, seed=SEED, precision=prec, stream=stream)
+    hist = torch.zeros(g.n_edges * BINS, dtype=torch.int32, device="cuda")
+
+    def step():
+        hist.zero_()
+        p.simulate(DT, args.em_steps, M, BINS, hist, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    c0 = p.counts(stream)["particle_steps"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else None)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    elapsed = sum(launch_ms) / 1e3
+    ps = p.counts(stream)["particle_steps"] - c0
+    if dist:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        s = torch.tensor([ps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(s)
+        ps = int(s.item())
+    value = ps / elapsed
+    per_launch = ps / (world * args.steps)
+    achieved = I_ALG * per_launch / (statistics.mean(launch_ms) / 1e3) / 1e12  # Tinst/s
+    props = torch.cuda.get_device_properties(local)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+                "frac": achieved / peak, "traffic": _traffic(kernel_hash()),
+                "note": f"{I_ALG} algorithmic thread-instructions per particle-step (fast path) x "
+                        f"particle-steps per launch / mean launch time; peak = "
+                        f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        he = torch.from_numpy(e0).pin_memory()
+        hx = torch.from_numpy(x0).pin_memory()
+        hh = np.zeros(g.n_edges * BINS, np.uint32)
+        e2e_steps = max(1, min(args.steps, 3))
+        times, eps = [], 0
+        for k in range(e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.reset(he.numpy(), hx.numpy(), stream)
+            p.simulate(DT, args.em_steps, M, 0, None, stream)
+            p.histogram(BINS, hh, stream)
+            cnt = p.counts(stream)
+            dt_ = time.perf_counter() - t0
+            if k > 0:  # first round warms the allocator and the host pages
+                times.append(dt_)
+                eps += cnt["particle_steps"]
+        h2d = int(he.numel() * 4 + hx.numel() * 8)
+        d2h = int(hh.nbytes + 8 * (g.n_slots + g.n_vertices + 2))
+        e2e = {"value": eps / sum(times) * world, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if pool is not None:
+        ps_c, t_c = cpu_oracle(desc, ce, cx, args.cpu_sample, args.em_steps, pool, cores)
+        pool.close()
+        cpu = {"value": ps_c / t_c, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} particles x {args.em_steps} EM-Steps of the same "
+                         f"workload (pids 0..{args.cpu_sample - 1}), FP64 oracle, one process "
+                         f"per core"}
+    counts = p.counts(stream)
+    p.close()
+    g.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": clk,
+            "launch_ms": launch_ms,
+            "truncations": counts["truncations"],
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

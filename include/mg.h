@@ -1,0 +1,221 @@
+/*
+ * mg.h -- C ABI of libmetricgraph: the timestep-splitting Euler-Maruyama
+ * scheme for diffusions on metric graphs ("Sampling on Metric Graphs",
+ * arXiv 2512.02175), run on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions (every entry point):
+ *  - Returns an mg_status; no C++ exception crosses this boundary.  On an
+ *    error, mg_last_error() returns a message for the calling thread.
+ *  - Pointers marked "host" are caller-owned host memory, read (or written)
+ *    only during the call.  Pointers marked "device" are caller-owned device
+ *    memory on the current CUDA device.  Handles (mg_graph, mg_particles) are
+ *    library-owned and freed by their _destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *    stream).  Calls that take a stream are stream-ordered and may return
+ *    before the GPU work finishes; errors found on the GPU are reported by the
+ *    next mg_synchronize or by any call that reads results back.
+ *  - Device memory is obtained through the allocator set by
+ *    mg_set_allocator (default: cudaMalloc/cudaFree).
+ *  - Floating-point inputs are IEEE binary64.  Integers are fixed width.
+ *
+ * Notation follows the paper: a metric graph (V, E, l) has edges e identified
+ * with intervals (0, l_e); e_init and e_term are the vertices at x = 0 and
+ * x = l_e (Definition 1).  A particle is a pair (e, x).  b_v is the
+ * vertex-edge jump distribution of the standard gluing conditions
+ * (Definition 4); E(v) is the set of edges incident to v.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_graph_s* mg_graph;
+typedef struct mg_particles_s* mg_particles;
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* an argument violates the stated contract */
+  MG_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL */
+  MG_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in mg_last_error) */
+  MG_ERR_TIMEOUT = 4,       /* a bounded wait ran out */
+  MG_ERR_CANCELLED = 5,     /* work was cancelled by the caller */
+  MG_ERR_BUSY = 6,          /* the handle is still referenced */
+  MG_ERR_DEVICE_FAULT = 7   /* a kernel flagged an invariant violation */
+} mg_status;
+
+typedef enum {
+  MG_FP64 = 0,      /* every step in binary64 */
+  MG_FP32_MIXED = 1 /* positions, increments and normals in binary32; the
+                       hitting fraction and remaining time of a split in
+                       binary64; counts in integers */
+} mg_precision;
+
+typedef enum { MG_VERTEX_STANDARD = 0, MG_VERTEX_ABSORBING = 1 } mg_vertex_kind;
+
+/* Device-error bits reported with MG_ERR_DEVICE_FAULT. */
+#define MG_DEVERR_BAD_EDGE 1u  /* a particle's edge index out of range */
+#define MG_DEVERR_NAN 2u       /* a position became NaN or left [0, l_e] */
+
+/* Description of a metric graph (Definition 1; drift and diffusion of the
+ * edge generator, Eq. (generator_edge); jump weights of the standard
+ * gluing conditions, Definition 4).  All arrays host, length n_edges unless
+ * noted; copied by mg_graph_create. */
+typedef struct {
+  int32_t n_vertices;          /* >= 1 */
+  int32_t n_edges;             /* >= 1 */
+  const int32_t* edge_src;     /* e_init in [0, n_vertices) */
+  const int32_t* edge_dst;     /* e_term in [0, n_vertices), or -1: the edge is
+                                  semi-infinite (a vertex at infinity) */
+  const double* length;        /* l_e > 0 finite; +INFINITY iff edge_dst == -1 */
+  const double* drift_c0;      /* mu_e(x) = c0 + c1 x, x measured from e_init */
+  const double* drift_c1;
+  const double* sigma;         /* diffusion sigma_e > 0, constant on the edge */
+  const double* weight_init;   /* >= 0: unnormalised b_{v e} at v = e_init */
+  const double* weight_term;   /* >= 0: unnormalised b_{v e} at v = e_term
+                                  (ignored for semi-infinite edges) */
+  const double* hist_range;    /* NULL, or > 0 finite: the histogram covers
+                                  [0, hist_range_e); NULL means l_e (1 for a
+                                  semi-infinite edge) */
+  const uint8_t* vertex_kind;  /* [n_vertices] mg_vertex_kind, or NULL (all
+                                  standard) */
+} mg_graph_desc;
+
+/* ---------------------------------------------------------------- memory */
+
+/* Allocation hooks (e.g. a framework's caching allocator).  alloc returns
+ * device memory of at least `bytes` bytes usable on `stream`, or NULL;
+ * free releases it.  Passing NULL for both restores cudaMalloc/cudaFree.
+ * Set before creating handles; memory is freed with the hooks that
+ * allocated it. */
+typedef void* (*mg_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*mg_free_fn)(void* ptr, void* stream, void* ctx);
+mg_status mg_set_allocator(mg_alloc_fn alloc, mg_free_fn free_fn, void* ctx);
+
+/* ----------------------------------------------------------------- graph */
+
+/* Validates `desc`, builds the incident-edge table ("slots": one per
+ * (vertex, incident edge end), ordered by vertex, then edge id, then init end
+ * before term end; a self-loop has two) and the integer jump thresholds that
+ * sample b_v (T_j = floor(2^32 C_j) from the binary64 running sums C_j of the
+ * normalised weights of v's slots, the last forced to 2^32; slot j is the
+ * first with u < T_j for a uniform 32-bit u), and uploads them to the current
+ * device.  MG_ERR_INVALID_ARG for: a vertex id out of range; a length <= 0 or
+ * NaN, infinite on a finite edge or finite on a semi-infinite one; sigma <= 0;
+ * a non-finite drift; a negative weight; a standard vertex with incident
+ * slots whose weights sum to 0; a bad hist_range or vertex kind. */
+mg_status mg_graph_create(const mg_graph_desc* desc, mg_graph* out);
+
+/* MG_ERR_BUSY while particle sets created on the graph are alive. */
+mg_status mg_graph_destroy(mg_graph g);
+
+/* Sizes of the graph: any output pointer may be NULL. */
+mg_status mg_graph_info(mg_graph g, int32_t* n_vertices, int32_t* n_edges, int32_t* n_slots);
+
+/* Copies the slot table to host arrays: vtx_off[n_vertices + 1] (slots of v
+ * are vtx_off[v] .. vtx_off[v+1]-1), slot_edge[n_slots], slot_end[n_slots]
+ * (0 init, 1 term), slot_threshold[n_slots] (T_j in [0, 2^32]).  Any pointer
+ * may be NULL. */
+mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge, uint8_t* slot_end,
+                         uint64_t* slot_threshold);
+
+/* ------------------------------------------------------------- particles */
+
+/* Creates a set of n particles on g (1 <= n <= 2^31 - 1).  edge0[n], x0[n]:
+ * starting edges and positions, host arrays, or device arrays when
+ * inputs_on_device != 0; 0 <= x0 <= l_e (x0 = 0 or l_e starts the particle at
+ * that vertex).  Particle i has the global id pid_base + i (must not wrap
+ * 2^32): its random numbers are Philox-4x32-10 (Salmon et al., SC'11) blocks
+ * under the key (seed mod 2^32, seed >> 32) with counters
+ *   (t >> 2, pid, 0, instance_id) for the normal of step t (lane t & 3) and
+ *   (j, pid, 1, instance_id)      for the draws of its j-th vertex hit,
+ * so results do not depend on how particles are sharded or batched.  The
+ * state holds, per particle: edge (-1 once absorbed), position x, hits,
+ * first_hits (hits that started inside the edge), flags (bit 0: the FP64
+ * trajectory passed within 1e-9 max(1, l_e) of a branch).  Step counter and
+ * all counters start at 0.  Host inputs are validated
+ * (MG_ERR_INVALID_ARG); device inputs are validated by the kernel. */
+mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edge0, const double* x0,
+                            int inputs_on_device, uint32_t pid_base, uint64_t seed,
+                            uint32_t instance_id, mg_precision precision, void* stream,
+                            mg_particles* out);
+
+/* Re-initialises the positions of an existing set (same n, graph, seed,
+ * precision) from edge0/x0 as in mg_particles_init, and zeroes its per-particle
+ * counters, step counter and global counters. */
+mg_status mg_particles_reset(mg_particles p, const int32_t* edge0, const double* x0,
+                             int inputs_on_device, void* stream);
+
+mg_status mg_particles_destroy(mg_particles p);
+
+/* Advances every particle by `steps` EM-Steps of length dt (Algorithm 2 of
+ * the paper, with sub-steps from a vertex taken into the edge with |W| as in
+ * Algorithm 1): an Euler-Maruyama sub-step x + mu_e(x) h + sigma_e sqrt(h) W;
+ * if it leaves the open interval (0, l_e), the partial step to the vertex
+ * (first root s = sqrt(alpha) in [0,1] of the sub-step's quadratic path),
+ * h <- (1 - alpha) h, the next edge drawn from b_v, and a new sub-step from
+ * that vertex; at most max_splits_M splits per step (a step that reaches M
+ * stays at the vertex and counts a truncation; Theorem 1); an absorbing
+ * vertex removes the particle.  Exits (a sub-step from a vertex that ends
+ * inside its edge), absorptions and truncations accumulate into the set's
+ * counters.  dt > 0 finite, steps >= 0, max_splits_M >= 1.
+ * If hist_bins > 0 and hist_out != NULL, the snapshot occupancy histogram of
+ * the final positions (as mg_histogram) is ADDED to the device array
+ * hist_out[n_edges * hist_bins] (uint32, caller-zeroed) in the same kernel.
+ * Stream-ordered. */
+mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
+                      int32_t hist_bins, uint32_t* hist_out, void* stream);
+
+/* Waits for the set's stream work and reports any device-error bits as
+ * MG_ERR_DEVICE_FAULT (the bits are in mg_last_error's message and are
+ * cleared). */
+mg_status mg_synchronize(mg_particles p);
+
+/* Snapshot occupancy histogram of the living particles: `bins` equal bins
+ * per edge over [0, hist_range_e); bin = min(floor(x * (bins / range_e)),
+ * bins - 1), computed in the set's precision.  out[n_edges * bins] uint32 is
+ * overwritten; it is device memory when out_on_device != 0 (stream-ordered),
+ * else host memory (the call synchronises). */
+mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, int out_on_device,
+                       void* stream);
+
+/* Copies the set's counters to host arrays (synchronises): slot_exits[n_slots]
+ * (in the slot order of mg_graph_slots), absorbed[n_vertices], truncations[1],
+ * particle_steps[1] (steps taken by living particles).  Any pointer may be
+ * NULL. */
+mg_status mg_exit_counts(mg_particles p, uint64_t* slot_exits, uint64_t* absorbed,
+                         uint64_t* truncations, uint64_t* particle_steps, void* stream);
+
+/* Zeroes the set's counters (stream-ordered). */
+mg_status mg_counters_reset(mg_particles p, void* stream);
+
+/* Checkpoint: copies the full particle state to host arrays (synchronises);
+ * positions are returned in binary64.  step: EM-Steps taken so far.  Any
+ * pointer may be NULL. */
+mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* hits,
+                       uint32_t* first_hits, uint32_t* flags, uint64_t* step, void* stream);
+
+/* Resume: overwrites the particle state from host arrays (all required) and
+ * the step counter; with the counter-based random numbers the continuation is
+ * bit-identical to an uninterrupted run. */
+mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x, const uint32_t* hits,
+                       const uint32_t* first_hits, const uint32_t* flags, uint64_t step,
+                       void* stream);
+
+/* n, precision and step counter of a set; any pointer may be NULL. */
+mg_status mg_particles_info(mg_particles p, int64_t* n, int32_t* precision, uint64_t* step);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* mg_last_error(void);
+
+/* Library version string. */
+const char* mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,76 @@
+// em_step_f32.cu -- binary32-mixed instantiation of the fused EM-Step kernel,
+// the histogram kernel and the state initialisation kernel.
+#include "mg_em_step.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+cudaError_t launch_em_step_f32(const SimArgs& a, size_t smem, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(em_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  const int64_t grid = (a.n + kBlock - 1) / kBlock;
+  em_step_kernel<false><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const void* x, int64_t n,
+                                 int32_t bins, uint32_t* out, bool smem, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  const size_t sh = smem ? align16((size_t)g.E * bins * 4) : 0;
+  if (sh > 48 * 1024)
+    cudaFuncSetAttribute(histogram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sh);
+  histogram_kernel<false><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
+  return cudaGetLastError();
+}
+
+__global__ void init_state_kernel(GraphView g, const int32_t* __restrict__ edge0,
+                                  const double* x0, int64_t n, int32_t f64, StateView s,
+                                  uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = edge0[i];
+    const double x = x0[i];  // may alias hits/first_hits: read before writing them
+    uint32_t bad = 0;
+    if (e < kDead || e >= g.E) bad |= kErrBadEdge;
+    else if (e >= 0 && !(x >= 0.0 && x <= g.e64[e].L)) bad |= kErrNan;
+    if (bad) atomicOr(err, bad);
+    s.edge[i] = e;
+    if (f64) reinterpret_cast<double*>(s.x)[i] = x;
+    else reinterpret_cast<float*>(s.x)[i] = (e >= 0 && x == g.e64[e].L) ? g.e32[e].L : (float)x;
+  }
+}
+
+__global__ void zero_counters_kernel(StateView s, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    s.hits[i] = 0u;
+    s.first_hits[i] = 0u;
+    s.flags[i] = 0u;
+  }
+}
+
+cudaError_t launch_init_state(const GraphView& g, const int32_t* edge0, const double* x0, int64_t n,
+                              bool f64, StateView s, uint32_t* err, cudaStream_t st) {
+  int64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  // x0 may live in the hits/first_hits storage: convert everything first,
+  // then zero the counters in a second, stream-ordered kernel.
+  init_state_kernel<<<(unsigned)grid, kBlock, 0, st>>>(g, edge0, x0, n, f64 ? 1 : 0, s, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  zero_counters_kernel<<<(unsigned)grid, kBlock, 0, st>>>(s, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,673 @@
+// mg_api.cpp -- the C ABI of libmetricgraph (declared in include/mg.h):
+// validation, graph tables, particle-set memory and kernel launches.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mg.h"
+#include "mg_launch.h"
+#include "mg_types.h"
+
+static_assert(MG_DEVERR_BAD_EDGE == mg::kErrBadEdge, "device error bits");
+static_assert(MG_DEVERR_NAN == mg::kErrNan, "device error bits");
+
+namespace {
+
+thread_local std::string g_err;
+
+mg_status fail(mg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+mg_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(MG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- memory
+
+std::mutex g_alloc_mu;
+mg_alloc_fn g_alloc = nullptr;
+mg_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  mg_free_fn free_fn = nullptr;  // hooks that allocated it (nullptr: cudaFree)
+  void* ctx = nullptr;
+};
+
+mg_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  b.bytes = bytes;
+  if (g_alloc) {
+    b.p = g_alloc(bytes, (void*)st, g_alloc_ctx);
+    b.free_fn = g_free;
+    b.ctx = g_alloc_ctx;
+    if (!b.p) return fail(MG_ERR_OUT_OF_MEMORY, "allocator hook returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      cudaGetLastError();
+      return fail(MG_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  return MG_OK;
+}
+
+void dev_free(DevBuf& b, cudaStream_t st) {
+  if (!b.p) return;
+  if (b.free_fn) b.free_fn(b.p, (void*)st, b.ctx);
+  else cudaFree(b.p);
+  b.p = nullptr;
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ graph
+
+struct mg_graph_s {
+  int32_t V = 0, E = 0, S = 0;
+  // host copies
+  std::vector<int32_t> src, dst, vtx_off, slot_edge, slot_of_end;
+  std::vector<uint8_t> slot_end, kind;
+  std::vector<uint64_t> slot_T;
+  std::vector<double> length, range;
+  // device tables (one allocation)
+  DevBuf buf;
+  mg::GraphView view{};
+  size_t table_bytes32 = 0, table_bytes64 = 0;
+  std::atomic<int> refs{0};
+};
+
+namespace {
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" mg_status mg_set_allocator(mg_alloc_fn alloc, mg_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(MG_ERR_INVALID_ARG, "mg_set_allocator: give both hooks or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
+  if (!d || !out) return fail(MG_ERR_INVALID_ARG, "mg_graph_create: NULL argument");
+  *out = nullptr;
+  const int32_t V = d->n_vertices, E = d->n_edges;
+  if (V < 1 || E < 1) return fail(MG_ERR_INVALID_ARG, "need n_vertices >= 1 and n_edges >= 1");
+  if (!d->edge_src || !d->edge_dst || !d->length || !d->drift_c0 || !d->drift_c1 || !d->sigma ||
+      !d->weight_init || !d->weight_term)
+    return fail(MG_ERR_INVALID_ARG, "mg_graph_create: a required array is NULL");
+  for (int32_t e = 0; e < E; ++e) {
+    const int32_t s = d->edge_src[e], t = d->edge_dst[e];
+    if (s < 0 || s >= V) return fail(MG_ERR_INVALID_ARG, "edge %d: src %d out of range", e, s);
+    if (t < -1 || t >= V) return fail(MG_ERR_INVALID_ARG, "edge %d: dst %d out of range", e, t);
+    const double L = d->length[e];
+    if (t == -1) {
+      if (!(std::isinf(L) && L > 0))
+        return fail(MG_ERR_INVALID_ARG, "edge %d: a semi-infinite edge needs length +inf", e);
+    } else if (!finite_pos(L)) {
+      return fail(MG_ERR_INVALID_ARG, "edge %d: length must be finite and > 0", e);
+    }
+    if (!finite_pos(d->sigma[e])) return fail(MG_ERR_INVALID_ARG, "edge %d: sigma must be > 0", e);
+    if (!std::isfinite(d->drift_c0[e]) || !std::isfinite(d->drift_c1[e]))
+      return fail(MG_ERR_INVALID_ARG, "edge %d: drift must be finite", e);
+    if (!(std::isfinite(d->weight_init[e]) && d->weight_init[e] >= 0.0))
+      return fail(MG_ERR_INVALID_ARG, "edge %d: weight_init must be >= 0", e);
+    if (t >= 0 && !(std::isfinite(d->weight_term[e]) && d->weight_term[e] >= 0.0))
+      return fail(MG_ERR_INVALID_ARG, "edge %d: weight_term must be >= 0", e);
+    if (d->hist_range && !finite_pos(d->hist_range[e]))
+      return fail(MG_ERR_INVALID_ARG, "edge %d: hist_range must be finite and > 0", e);
+  }
+  if (d->vertex_kind)
+    for (int32_t v = 0; v < V; ++v)
+      if (d->vertex_kind[v] > MG_VERTEX_ABSORBING)
+        return fail(MG_ERR_INVALID_ARG, "vertex %d: unknown kind %d", v, d->vertex_kind[v]);
+
+  mg_graph g = new mg_graph_s();
+  g->V = V;
+  g->E = E;
+  g->src.assign(d->edge_src, d->edge_src + E);
+  g->dst.assign(d->edge_dst, d->edge_dst + E);
+  g->length.assign(d->length, d->length + E);
+  g->range.resize(E);
+  for (int32_t e = 0; e < E; ++e)
+    g->range[e] = d->hist_range ? d->hist_range[e] : (g->dst[e] >= 0 ? g->length[e] : 1.0);
+  g->kind.assign(V, 0);
+  if (d->vertex_kind) g->kind.assign(d->vertex_kind, d->vertex_kind + V);
+
+  // Slots by counting sort on the vertex: each edge contributes its init end
+  // then its term end, edges in id order, so within a vertex the slots are
+  // ordered by (edge id, init before term).
+  std::vector<int32_t> deg(V + 1, 0);
+  for (int32_t e = 0; e < E; ++e) {
+    deg[g->src[e]]++;
+    if (g->dst[e] >= 0) deg[g->dst[e]]++;
+  }
+  g->vtx_off.assign(V + 1, 0);
+  for (int32_t v = 0; v < V; ++v) g->vtx_off[v + 1] = g->vtx_off[v] + deg[v];
+  const int32_t S = g->vtx_off[V];
+  g->S = S;
+  g->slot_edge.assign(S, 0);
+  g->slot_end.assign(S, 0);
+  g->slot_T.assign(S, 0);
+  g->slot_of_end.assign(2 * (size_t)E, -1);
+  std::vector<double> w(S, 0.0);
+  std::vector<int32_t> fill(g->vtx_off.begin(), g->vtx_off.end() - 1);
+  for (int32_t e = 0; e < E; ++e) {
+    int32_t j = fill[g->src[e]]++;
+    g->slot_edge[j] = e;
+    g->slot_end[j] = mg::kEndInit;
+    w[j] = d->weight_init[e];
+    g->slot_of_end[2 * (size_t)e] = j;
+    if (g->dst[e] >= 0) {
+      j = fill[g->dst[e]]++;
+      g->slot_edge[j] = e;
+      g->slot_end[j] = mg::kEndTerm;
+      w[j] = d->weight_term[e];
+      g->slot_of_end[2 * (size_t)e + 1] = j;
+    }
+  }
+  // Integer thresholds of b_v: T_j = min(floor(2^32 C_j), 2^32) with C_j the
+  // binary64 running sum of v's weights divided by their binary64 total; the
+  // last slot of v gets 2^32.
+  for (int32_t v = 0; v < V; ++v) {
+    const int32_t lo = g->vtx_off[v], hi = g->vtx_off[v + 1];
+    if (lo == hi) continue;
+    double tot = 0.0;
+    for (int32_t j = lo; j < hi; ++j) tot += w[j];
+    if (g->kind[v] == MG_VERTEX_STANDARD && !(tot > 0.0)) {
+      delete g;
+      return fail(MG_ERR_INVALID_ARG, "vertex %d: jump weights sum to 0", v);
+    }
+    double cum = 0.0;
+    for (int32_t j = lo; j < hi; ++j) {
+      cum += w[j];
+      const double c = (tot > 0.0) ? cum / tot : 1.0;
+      const double f = std::floor(c * 4294967296.0);
+      g->slot_T[j] = (f >= 4294967296.0) ? 4294967296ull : (uint64_t)f;
+    }
+    g->slot_T[hi - 1] = 4294967296ull;
+  }
+
+  // device tables
+  std::vector<mg::EdgeRec32> e32(E);
+  std::vector<mg::EdgeRec64> e64(E);
+  for (int32_t e = 0; e < E; ++e) {
+    const double L = g->length[e];
+    e64[e] = {L, d->drift_c0[e], d->drift_c1[e], d->sigma[e], g->src[e], g->dst[e],
+              g->slot_of_end[2 * (size_t)e], g->slot_of_end[2 * (size_t)e + 1]};
+    e32[e] = {(float)L, (float)d->drift_c0[e], (float)d->drift_c1[e], (float)d->sigma[e],
+              g->src[e], g->dst[e], g->slot_of_end[2 * (size_t)e],
+              g->slot_of_end[2 * (size_t)e + 1]};
+  }
+  std::vector<mg::SlotRec> slots(S);
+  for (int32_t j = 0; j < S; ++j) slots[j] = {g->slot_T[j], g->slot_edge[j], g->slot_end[j]};
+  std::vector<mg::VtxRec> vtx(V);
+  for (int32_t v = 0; v < V; ++v) vtx[v] = {g->vtx_off[v], g->vtx_off[v + 1], g->kind[v], 0};
+
+  const size_t o32 = 0, o64 = a256(o32 + E * sizeof(mg::EdgeRec32));
+  const size_t os = a256(o64 + E * sizeof(mg::EdgeRec64));
+  const size_t ov = a256(os + S * sizeof(mg::SlotRec));
+  const size_t orr = a256(ov + V * sizeof(mg::VtxRec));
+  const size_t total = a256(orr + E * sizeof(double));
+  mg_status st = dev_alloc(g->buf, total, nullptr);
+  if (st != MG_OK) {
+    delete g;
+    return st;
+  }
+  std::vector<unsigned char> host(total, 0);
+  memcpy(host.data() + o32, e32.data(), E * sizeof(mg::EdgeRec32));
+  memcpy(host.data() + o64, e64.data(), E * sizeof(mg::EdgeRec64));
+  memcpy(host.data() + os, slots.data(), S * sizeof(mg::SlotRec));
+  memcpy(host.data() + ov, vtx.data(), V * sizeof(mg::VtxRec));
+  memcpy(host.data() + orr, g->range.data(), E * sizeof(double));
+  cudaError_t ce = cudaMemcpy(g->buf.p, host.data(), total, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    dev_free(g->buf, nullptr);
+    delete g;
+    return cuda_fail(ce, "mg_graph_create: upload");
+  }
+  unsigned char* base = static_cast<unsigned char*>(g->buf.p);
+  g->view.V = V;
+  g->view.E = E;
+  g->view.S = S;
+  g->view.e32 = reinterpret_cast<const mg::EdgeRec32*>(base + o32);
+  g->view.e64 = reinterpret_cast<const mg::EdgeRec64*>(base + o64);
+  g->view.slot = reinterpret_cast<const mg::SlotRec*>(base + os);
+  g->view.vtx = reinterpret_cast<const mg::VtxRec*>(base + ov);
+  g->view.range = reinterpret_cast<const double*>(base + orr);
+  *out = g;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_destroy(mg_graph g) {
+  if (!g) return MG_OK;
+  if (g->refs.load() > 0)
+    return fail(MG_ERR_BUSY, "mg_graph_destroy: %d particle sets still use the graph",
+                g->refs.load());
+  dev_free(g->buf, nullptr);
+  delete g;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_info(mg_graph g, int32_t* V, int32_t* E, int32_t* S) {
+  if (!g) return fail(MG_ERR_INVALID_ARG, "mg_graph_info: NULL graph");
+  if (V) *V = g->V;
+  if (E) *E = g->E;
+  if (S) *S = g->S;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge,
+                                    uint8_t* slot_end, uint64_t* slot_threshold) {
+  if (!g) return fail(MG_ERR_INVALID_ARG, "mg_graph_slots: NULL graph");
+  if (vtx_off) memcpy(vtx_off, g->vtx_off.data(), (g->V + 1) * sizeof(int32_t));
+  if (slot_edge) memcpy(slot_edge, g->slot_edge.data(), g->S * sizeof(int32_t));
+  if (slot_end) memcpy(slot_end, g->slot_end.data(), g->S);
+  if (slot_threshold) memcpy(slot_threshold, g->slot_T.data(), g->S * sizeof(uint64_t));
+  return MG_OK;
+}
+
+// -------------------------------------------------------------- particles
+
+struct mg_particles_s {
+  mg_graph g = nullptr;
+  int64_t n = 0;
+  uint32_t pid_base = 0;
+  uint64_t seed = 0;
+  uint32_t instance = 0;
+  mg_precision prec = MG_FP64;
+  uint64_t step = 0;
+  DevBuf state;      // edge | x | hits | first_hits | flags
+  DevBuf counters;   // exits[S] | absorbed[V] | trunc | psteps | err
+  DevBuf hist_tmp;   // histogram staging for host output
+  mg::StateView sv{};
+  mg::CounterView cv{};
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+size_t xbytes(const mg_particles_s* p) { return p->prec == MG_FP64 ? 8 : 4; }
+
+void state_layout(mg_particles_s* p) {
+  const int64_t n = p->n;
+  unsigned char* b = static_cast<unsigned char*>(p->state.p);
+  size_t o = 0;
+  p->sv.edge = reinterpret_cast<int32_t*>(b + o);
+  o = a256(o + 4 * (size_t)n);
+  p->sv.x = b + o;
+  o = a256(o + xbytes(p) * (size_t)n);
+  // hits and first_hits are adjacent: 8n contiguous bytes, 8-byte aligned,
+  // reused as the binary64 staging area of host positions at initialisation
+  p->sv.hits = reinterpret_cast<uint32_t*>(b + o);
+  p->sv.first_hits = p->sv.hits + n;
+  o = a256(o + 8 * (size_t)n);
+  p->sv.flags = reinterpret_cast<uint32_t*>(b + o);
+}
+
+size_t state_bytes(int64_t n, size_t xb) {
+  return a256(4 * (size_t)n) + a256(xb * (size_t)n) + a256(8 * (size_t)n) + a256(4 * (size_t)n);
+}
+
+void counter_layout(mg_particles_s* p) {
+  unsigned char* b = static_cast<unsigned char*>(p->counters.p);
+  size_t o = 0;
+  p->cv.exits = reinterpret_cast<unsigned long long*>(b + o);
+  o += 8 * (size_t)p->g->S;
+  p->cv.absorbed = reinterpret_cast<unsigned long long*>(b + o);
+  o += 8 * (size_t)p->g->V;
+  p->cv.trunc = reinterpret_cast<unsigned long long*>(b + o);
+  o += 8;
+  p->cv.psteps = reinterpret_cast<unsigned long long*>(b + o);
+  o += 8;
+  p->cv.err = reinterpret_cast<uint32_t*>(b + o);
+}
+
+size_t counter_bytes(const mg_graph g) { return 8 * ((size_t)g->S + g->V + 2) + 16; }
+
+mg_status load_positions(mg_particles p, const int32_t* edge0, const double* x0, int on_device,
+                         cudaStream_t st) {
+  const int64_t n = p->n;
+  const mg_graph g = p->g;
+  if (!edge0 || !x0) return fail(MG_ERR_INVALID_ARG, "edge0 and x0 are required");
+  const int32_t* dedge = edge0;
+  const double* dx = x0;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t e = edge0[i];
+      if (e < 0 || e >= g->E)
+        return fail(MG_ERR_INVALID_ARG, "particle %lld: edge %d out of range", (long long)i, e);
+      const double x = x0[i];
+      if (!(x >= 0.0 && x <= g->length[e]))
+        return fail(MG_ERR_INVALID_ARG, "particle %lld: x0 outside [0, l_e]", (long long)i);
+    }
+    // edges straight into place; positions into the 8n bytes of hits and
+    // first_hits (binary64 staging), converted by the init kernel
+    MG_CUDA(cudaMemcpyAsync(p->sv.edge, edge0, 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    MG_CUDA(cudaMemcpyAsync(p->sv.hits, x0, 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+    dedge = p->sv.edge;
+    dx = reinterpret_cast<const double*>(p->sv.hits);
+  }
+  MG_CUDA(mg::launch_init_state(g->view, dedge, dx, n, p->prec == MG_FP64, p->sv, p->cv.err, st));
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edge0,
+                                       const double* x0, int inputs_on_device, uint32_t pid_base,
+                                       uint64_t seed, uint32_t instance_id,
+                                       mg_precision precision, void* stream, mg_particles* out) {
+  if (!g || !out) return fail(MG_ERR_INVALID_ARG, "mg_particles_init: NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > 2147483647LL) return fail(MG_ERR_INVALID_ARG, "need 1 <= n <= 2^31 - 1");
+  if ((uint64_t)pid_base + (uint64_t)n > 4294967296ull)
+    return fail(MG_ERR_INVALID_ARG, "pid_base + n exceeds 2^32");
+  if (precision != MG_FP64 && precision != MG_FP32_MIXED)
+    return fail(MG_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mg_particles p = new mg_particles_s();
+  p->g = g;
+  p->n = n;
+  p->pid_base = pid_base;
+  p->seed = seed;
+  p->instance = instance_id;
+  p->prec = precision;
+  mg_status s = dev_alloc(p->state, state_bytes(n, xbytes(p)), st);
+  if (s == MG_OK) s = dev_alloc(p->counters, counter_bytes(g), st);
+  if (s != MG_OK) {
+    dev_free(p->state, st);
+    delete p;
+    return s;
+  }
+  state_layout(p);
+  counter_layout(p);
+  cudaError_t ce = cudaMemsetAsync(p->counters.p, 0, counter_bytes(g), st);
+  if (ce != cudaSuccess) s = cuda_fail(ce, "mg_particles_init: memset");
+  if (s == MG_OK) s = load_positions(p, edge0, x0, inputs_on_device, st);
+  if (s != MG_OK) {
+    dev_free(p->state, st);
+    dev_free(p->counters, st);
+    delete p;
+    return s;
+  }
+  p->last_stream = st;
+  g->refs++;
+  *out = p;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_particles_reset(mg_particles p, const int32_t* edge0, const double* x0,
+                                        int inputs_on_device, void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_particles_reset: NULL particles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_CUDA(cudaMemsetAsync(p->counters.p, 0, counter_bytes(p->g), st));
+  mg_status s = load_positions(p, edge0, x0, inputs_on_device, st);
+  if (s != MG_OK) return s;
+  p->step = 0;
+  p->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_particles_destroy(mg_particles p) {
+  if (!p) return MG_OK;
+  cudaStreamSynchronize(p->last_stream);
+  dev_free(p->state, p->last_stream);
+  dev_free(p->counters, p->last_stream);
+  dev_free(p->hist_tmp, p->last_stream);
+  p->g->refs--;
+  delete p;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_particles_info(mg_particles p, int64_t* n, int32_t* precision,
+                                       uint64_t* step) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_particles_info: NULL particles");
+  if (n) *n = p->n;
+  if (precision) *precision = (int32_t)p->prec;
+  if (step) *step = p->step;
+  return MG_OK;
+}
+
+namespace {
+
+// Largest dynamic shared memory the fused kernel may take per block while
+// keeping up to 8 resident blocks of 256 threads on an SM.
+constexpr size_t kSmemBudget = 24 * 1024;
+
+}  // namespace
+
+extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t M,
+                                 int32_t hist_bins, uint32_t* hist_out, void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_simulate: NULL particles");
+  if (!(std::isfinite(dt) && dt > 0.0)) return fail(MG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (steps < 0) return fail(MG_ERR_INVALID_ARG, "steps must be >= 0");
+  if (M < 1) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be >= 1");
+  if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");
+  if (hist_bins > 0 && !hist_out) return fail(MG_ERR_INVALID_ARG, "hist_bins > 0 needs hist_out");
+  // the step index t enters the Philox counter as t >> 2 in 32 bits
+  if (p->step + (uint64_t)steps > (1ull << 34))
+    return fail(MG_ERR_INVALID_ARG, "step counter would exceed 2^34");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mg_graph g = p->g;
+  const bool f64 = p->prec == MG_FP64;
+
+  mg::SimArgs a{};
+  a.g = g->view;
+  a.s = p->sv;
+  a.c = p->cv;
+  a.n = p->n;
+  a.pid_base = p->pid_base;
+  a.instance = p->instance;
+  const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {
+    a.rk[2 * r] = k0 + r * 0x9E3779B9u;
+    a.rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
+  }
+  a.dt = dt;
+  a.sqrt_dt = std::sqrt(dt);
+  a.M = M;
+  // shared-memory plan: stage the tables, then the counters, then the
+  // histogram, as long as the total stays within the budget
+  const bool want_hist = hist_bins > 0;
+  const int32_t hist_len = want_hist ? g->E * hist_bins : 0;
+  bool stage = true, counters = true, shist = want_hist;
+  auto lay = [&]() {
+    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters, shist ? hist_len : 0).total;
+  };
+  if (lay() > kSmemBudget) shist = false;
+  if (lay() > kSmemBudget) counters = false;
+  if (lay() > kSmemBudget) stage = false;
+  if (lay() > kSmemBudget) counters = false;
+  a.stage_smem = stage;
+  a.smem_counters = counters;
+  a.smem_hist = shist;
+  const size_t smem = lay();
+  // 32-bit shared counters: a block of 256 particles adds at most 256 M per
+  // step to one counter; split the launch so that cannot wrap
+  int64_t chunk = steps;
+  if (counters) {
+    const int64_t cap = (int64_t)(4294967295ull / (256ull * (uint64_t)M));
+    if (chunk > cap) chunk = cap;
+  }
+  if (chunk < 1) chunk = 1;
+  int64_t done = 0;
+  do {
+    const int64_t now = (steps - done < chunk) ? steps - done : chunk;
+    a.t_begin = p->step + (uint64_t)done;
+    a.steps = now;
+    const bool last = done + now >= steps;
+    a.hist_bins = (last && want_hist) ? hist_bins : 0;
+    a.hist = hist_out;
+    a.smem_hist = (last && shist) ? 1 : 0;
+    const size_t sm = (last && shist) ? smem
+                      : mg::smem_layout(g->V, g->E, g->S, f64, stage, counters, 0).total;
+    cudaError_t ce = f64 ? mg::launch_em_step_f64(a, sm, st) : mg::launch_em_step_f32(a, sm, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "mg_simulate: launch");
+    done += now;
+  } while (done < steps);
+  p->step += (uint64_t)steps;
+  p->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_synchronize(mg_particles p) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_synchronize: NULL particles");
+  MG_CUDA(cudaStreamSynchronize(p->last_stream));
+  uint32_t err = 0;
+  MG_CUDA(cudaMemcpy(&err, p->cv.err, 4, cudaMemcpyDeviceToHost));
+  if (err) {
+    MG_CUDA(cudaMemset(p->cv.err, 0, 4));
+    return fail(MG_ERR_DEVICE_FAULT, "device error bits 0x%x (1: edge out of range, 2: position "
+                "outside [0, l_e] or NaN)", err);
+  }
+  return MG_OK;
+}
+
+extern "C" mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, int out_on_device,
+                                  void* stream) {
+  if (!p || !out) return fail(MG_ERR_INVALID_ARG, "mg_histogram: NULL argument");
+  if (bins < 1) return fail(MG_ERR_INVALID_ARG, "bins must be >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mg_graph g = p->g;
+  const size_t bytes = (size_t)g->E * bins * 4;
+  uint32_t* dst = out;
+  if (!out_on_device) {
+    if (p->hist_tmp.bytes < bytes) {
+      dev_free(p->hist_tmp, st);
+      mg_status s = dev_alloc(p->hist_tmp, bytes, st);
+      if (s != MG_OK) return s;
+    }
+    dst = static_cast<uint32_t*>(p->hist_tmp.p);
+  }
+  MG_CUDA(cudaMemsetAsync(dst, 0, bytes, st));
+  const bool sm = bytes <= 96 * 1024;
+  cudaError_t ce = (p->prec == MG_FP64)
+                       ? mg::launch_histogram_f64(g->view, p->sv.edge, p->sv.x, p->n, bins, dst, sm, st)
+                       : mg::launch_histogram_f32(g->view, p->sv.edge, p->sv.x, p->n, bins, dst, sm, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "mg_histogram: launch");
+  p->last_stream = st;
+  if (!out_on_device) {
+    MG_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+  }
+  return MG_OK;
+}
+
+extern "C" mg_status mg_exit_counts(mg_particles p, uint64_t* slot_exits, uint64_t* absorbed,
+                                    uint64_t* truncations, uint64_t* particle_steps, void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_exit_counts: NULL particles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mg_graph g = p->g;
+  std::vector<uint64_t> h(counter_bytes(g) / 8 + 1, 0);
+  MG_CUDA(cudaMemcpyAsync(h.data(), p->counters.p, 8 * ((size_t)g->S + g->V + 2),
+                          cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  if (slot_exits) memcpy(slot_exits, h.data(), 8 * (size_t)g->S);
+  if (absorbed) memcpy(absorbed, h.data() + g->S, 8 * (size_t)g->V);
+  if (truncations) *truncations = h[g->S + g->V];
+  if (particle_steps) *particle_steps = h[g->S + g->V + 1];
+  return MG_OK;
+}
+
+extern "C" mg_status mg_counters_reset(mg_particles p, void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_counters_reset: NULL particles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_CUDA(cudaMemsetAsync(p->counters.p, 0, 8 * ((size_t)p->g->S + p->g->V + 2), st));
+  p->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* hits,
+                                  uint32_t* first_hits, uint32_t* flags, uint64_t* step,
+                                  void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_state_get: NULL particles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)p->n;
+  if (edge) MG_CUDA(cudaMemcpyAsync(edge, p->sv.edge, 4 * n, cudaMemcpyDeviceToHost, st));
+  std::vector<float> xf;
+  if (x) {
+    if (p->prec == MG_FP64) {
+      MG_CUDA(cudaMemcpyAsync(x, p->sv.x, 8 * n, cudaMemcpyDeviceToHost, st));
+    } else {
+      xf.resize(n);
+      MG_CUDA(cudaMemcpyAsync(xf.data(), p->sv.x, 4 * n, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (hits) MG_CUDA(cudaMemcpyAsync(hits, p->sv.hits, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (first_hits)
+    MG_CUDA(cudaMemcpyAsync(first_hits, p->sv.first_hits, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (flags) MG_CUDA(cudaMemcpyAsync(flags, p->sv.flags, 4 * n, cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  if (x && p->prec != MG_FP64)
+    for (size_t i = 0; i < n; ++i) x[i] = (double)xf[i];
+  if (step) *step = p->step;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x,
+                                  const uint32_t* hits, const uint32_t* first_hits,
+                                  const uint32_t* flags, uint64_t step, void* stream) {
+  if (!p || !edge || !x || !hits || !first_hits || !flags)
+    return fail(MG_ERR_INVALID_ARG, "mg_state_set: NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)p->n;
+  const mg_graph g = p->g;
+  for (size_t i = 0; i < n; ++i) {
+    const int32_t e = edge[i];
+    if (e < -1 || e >= g->E) return fail(MG_ERR_INVALID_ARG, "edge out of range");
+    if (e >= 0 && !(x[i] >= 0.0 && x[i] <= g->length[e]))
+      return fail(MG_ERR_INVALID_ARG, "x outside [0, l_e]");
+  }
+  std::vector<float> xf;
+  MG_CUDA(cudaMemcpyAsync(p->sv.edge, edge, 4 * n, cudaMemcpyHostToDevice, st));
+  if (p->prec == MG_FP64) {
+    MG_CUDA(cudaMemcpyAsync(p->sv.x, x, 8 * n, cudaMemcpyHostToDevice, st));
+  } else {
+    xf.resize(n);
+    for (size_t i = 0; i < n; ++i) xf[i] = (float)x[i];
+    MG_CUDA(cudaMemcpyAsync(p->sv.x, xf.data(), 4 * n, cudaMemcpyHostToDevice, st));
+  }
+  MG_CUDA(cudaMemcpyAsync(p->sv.hits, hits, 4 * n, cudaMemcpyHostToDevice, st));
+  MG_CUDA(cudaMemcpyAsync(p->sv.first_hits, first_hits, 4 * n, cudaMemcpyHostToDevice, st));
+  MG_CUDA(cudaMemcpyAsync(p->sv.flags, flags, 4 * n, cudaMemcpyHostToDevice, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  p->step = step;
+  p->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" const char* mg_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* mg_version(void) { return "libmetricgraph 0.1 (sm_103a)"; }

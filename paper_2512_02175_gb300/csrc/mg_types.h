@@ -1,0 +1,119 @@
+// mg_types.h -- device-side table layouts shared by the host builder and the
+// kernels of libmetricgraph (not part of the public C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define MG_HD __host__ __device__
+#else
+#define MG_HD
+#endif
+
+namespace mg {
+
+enum : int32_t { kEndInit = 0, kEndTerm = 1, kDead = -1 };
+enum : int32_t { kVertexStandard = 0, kVertexAbsorbing = 1 };
+// device-error bits (same values as MG_DEVERR_* in the public header)
+enum : uint32_t { kErrBadEdge = 1u, kErrNan = 2u };
+
+// One edge (Definition 1) with its drift mu_e(x) = c0 + c1 x and diffusion
+// sigma_e; 32 bytes so a warp loads it with one 16-byte pair per lane.
+struct alignas(16) EdgeRec32 {
+  float L, c0, c1, sigma;               // L = +inf for a semi-infinite edge
+  int32_t src, dst, slot_init, slot_term; // dst = -1: vertex at infinity
+};
+
+struct alignas(16) EdgeRec64 {
+  double L, c0, c1, sigma;
+  int32_t src, dst, slot_init, slot_term;
+};
+
+// One (vertex, incident edge end) with its integer jump threshold T in
+// [0, 2^32]: slot j of v is drawn when u < T_j and u >= T_{j-1}.
+struct alignas(16) SlotRec {
+  uint64_t T;
+  int32_t edge, end;
+};
+
+// Slots of vertex v are [begin, end); kind is mg_vertex_kind.
+struct alignas(16) VtxRec {
+  int32_t begin, end, kind, pad;
+};
+
+// Read-only view of a graph on the device (global memory, or shared memory
+// after staging).
+struct GraphView {
+  int32_t V, E, S;
+  const EdgeRec32* e32;
+  const EdgeRec64* e64;
+  const SlotRec* slot;
+  const VtxRec* vtx;
+  const double* range;  // histogram range per edge
+};
+
+// Particle state, structure of arrays.
+struct StateView {
+  int32_t* edge;
+  void* x;  // float* (FP32 mixed) or double* (FP64)
+  uint32_t* hits;
+  uint32_t* first_hits;
+  uint32_t* flags;
+};
+
+struct CounterView {
+  unsigned long long* exits;     // [S]
+  unsigned long long* absorbed;  // [V]
+  unsigned long long* trunc;     // [1]
+  unsigned long long* psteps;    // [1] particle-steps taken while alive
+  uint32_t* err;                 // [1] device-error bits
+};
+
+// Everything one launch of the fused EM-Step kernel needs.
+struct SimArgs {
+  GraphView g;
+  StateView s;
+  CounterView c;
+  int64_t n;
+  uint32_t pid_base;
+  uint32_t instance;
+  uint32_t rk[20];      // Philox round keys: (seed lo + r W0, seed hi + r W1), r = 0..9
+  uint64_t t_begin;     // global index of the first step of this launch
+  int64_t steps;
+  double dt, sqrt_dt;
+  int32_t M;
+  int32_t hist_bins;    // 0: no fused histogram
+  uint32_t* hist;       // [E * hist_bins]
+  int32_t stage_smem;   // graph tables staged in shared memory
+  int32_t smem_counters;// exit/absorbed counters privatised in shared memory
+  int32_t smem_hist;    // histogram privatised in shared memory
+};
+
+// Dynamic shared memory of the fused kernel: staged tables, privatised
+// counters, privatised histogram (each part optional).
+struct SmemLayout {
+  size_t edges, slots, vtx, exits, absorbed, hist, total;
+};
+
+MG_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
+                                                  bool stage, bool counters, int32_t hist_len) {
+  SmemLayout l{};
+  size_t off = 0;
+  if (stage) {
+    l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
+    l.slots = off; off += align16((size_t)S * sizeof(SlotRec));
+    l.vtx = off; off += align16((size_t)V * sizeof(VtxRec));
+  }
+  if (counters) {
+    l.exits = off; off += align16((size_t)S * 4);
+    l.absorbed = off; off += align16((size_t)V * 4);
+  }
+  l.hist = off;
+  off += align16((size_t)hist_len * 4);
+  l.total = off;
+  return l;
+}
+
+}  // namespace mg

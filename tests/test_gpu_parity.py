@@ -1,0 +1,344 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+* FP64 mode: trajectory by trajectory -- edge ids, hit counters and exit /
+  absorption / truncation counts identical; |x_gpu - x_oracle| <=
+  1e-12 max(1, |x|); particles whose trajectory passed within 1e-9 of a
+  branch (flag bit 0 on either side) are excluded, and counted.  The only
+  allowed differences are the ulp-level results of log / sin / cos on the two
+  sides, which a 1e-9 branch margin cannot turn into a different decision.
+* FP32-mixed mode: statistical -- per-edge occupancy and per-slot exit
+  frequencies within 3 standard errors of the oracle's (same Philox streams),
+  coupled final-edge agreement, and the histogram total-variation distance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_02175_gb300 import workloads as W
+from tests import oracle_pool
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    return B
+
+
+def gpu_run(B, desc, edge, x, *, seed, dt, steps, M, prec, pid_base=0, instance=0, chunks=None,
+            bins=0):
+    g = B.Graph(desc)
+    p = B.Particles(g, edge, x, pid_base=pid_base, seed=seed, instance=instance, precision=prec)
+    for c in (chunks or [steps]):
+        p.simulate(dt, c, M)
+    p.synchronize()
+    st = p.state()
+    cnt = p.counts()
+    hist = p.histogram(bins) if bins else None
+    p.close()
+    g.close()
+    return st, cnt, hist
+
+
+def assert_fp64_parity(gs, gc, o, *, max_flag_frac=0.01, ghist=None):
+    flagged = ((gs["flags"] & 1) | (o["flags"] & 1)) != 0
+    ok = ~flagged
+    assert flagged.mean() <= max_flag_frac, flagged.mean()
+    assert np.array_equal(gs["edge"][ok], o["edge"][ok])
+    assert np.array_equal(gs["hits"][ok], o["hits"][ok])
+    assert np.array_equal(gs["first_hits"][ok], o["first_hits"][ok])
+    dx = np.abs(gs["x"][ok] - o["x"][ok])
+    tol = REL * np.maximum(1.0, np.abs(o["x"][ok]))
+    assert np.all(dx <= tol), (dx.max(), np.argmax(dx - tol))
+    if not flagged.any():
+        assert np.array_equal(gc["exits"], o["exits"])
+        assert np.array_equal(gc["absorbed"], o["absorbed"])
+        assert gc["truncations"] == o["truncations"]
+        assert gc["particle_steps"] == o["particle_steps"]
+        if ghist is not None:
+            assert np.array_equal(ghist.astype(np.uint64), o["hist"])
+    else:
+        slack = int(gs["hits"][flagged].sum() + o["hits"][flagged].sum()) + int(flagged.sum())
+        assert np.abs(gc["exits"].astype(np.int64) - o["exits"].astype(np.int64)).sum() <= 2 * slack
+    return int(flagged.sum())
+
+
+# ------------------------------------------------------------ FP64 parity
+
+def test_star3_brownian_fp64_trajectories(B):
+    """The 3-edge Brownian star in full: N = 10^4, 1000 steps, M = 8."""
+    d = W.star_brownian(3)
+    e, x = W.round_robin_uniform(d, 10_000, 11)
+    gs, gc, gh = gpu_run(B, d, e, x, seed=0, dt=1e-3, steps=1000, M=8, prec=B.MG_FP64, bins=32)
+    o = oracle_pool.run(d, e, x, seed=0, dt=1e-3, steps=1000, M=8, bins=32)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+    assert gc["exits"].sum() > 100_000
+
+
+def test_mixed_graph_fp64_unaligned_chunks(B):
+    """Cycles, a self-loop, a semi-infinite edge, zero weights, absorbing
+    vertices, a small split cap (truncations), ids offset, steps in chunks
+    that start off a multiple of four."""
+    d = W.random_mixed(7)
+    e, x = W.uniform_on_edges(d, 4096, 3)
+    x[:64] = 0.0  # start at init vertices
+    kw = dict(seed=5, dt=5e-3, steps=300, M=3, pid_base=1000, instance=3)
+    gs, gc, gh = gpu_run(B, d, e, x, prec=B.MG_FP64, chunks=[7, 1, 290, 2], bins=8, **kw)
+    o = oracle_pool.run(d, e, x, np.arange(1000, 1000 + 4096), seed=5, instance=3, dt=5e-3,
+                        steps=300, M=3, bins=8)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+    assert gc["truncations"] > 0 and gc["absorbed"].sum() > 0
+
+
+def test_random_tree_fp64_from_vertices(B):
+    d = W.random_tree(300, seed=4)
+    e, x = W.uniform_on_edges(d, 8192, 8)
+    x[::5] = 0.0
+    x[1::5] = d["length"][e[1::5]]  # start at term vertices
+    gs, gc, gh = gpu_run(B, d, e, x, seed=9, dt=2e-3, steps=200, M=16, prec=B.MG_FP64, bins=4)
+    o = oracle_pool.run(d, e, x, seed=9, dt=2e-3, steps=200, M=16, bins=4)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+
+
+def test_large_graph_global_tables_fp64(B):
+    """A graph too large for shared-memory staging: tables read through L2,
+    counters with global atomics."""
+    d = W.random_tree(6000, seed=12)
+    e, x = W.uniform_on_edges(d, 8192, 2)
+    gs, gc, gh = gpu_run(B, d, e, x, seed=1, dt=4e-3, steps=150, M=8, prec=B.MG_FP64, bins=2)
+    o = oracle_pool.run(d, e, x, seed=1, dt=4e-3, steps=150, M=8, bins=2)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+
+
+def test_paper_star_semi_infinite_fp64(B):
+    """The paper's 5-edge semi-infinite star, linear potential mu_i = -10 i."""
+    d = W.paper_star("linear")
+    n = 4096
+    e = (np.arange(n) % 5).astype(np.int32)
+    x = np.random.default_rng(0).exponential(0.05, n)
+    gs, gc, gh = gpu_run(B, d, e, x, seed=3, dt=1e-4, steps=500, M=16, prec=B.MG_FP64, bins=16)
+    o = oracle_pool.run(d, e, x, seed=3, dt=1e-4, steps=500, M=16, bins=16)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+
+
+def test_edge_cases_fp64(B):
+    d = W.star_brownian(3)
+    # one particle; zero steps leaves it untouched
+    gs, gc, _ = gpu_run(B, d, [1], [0.25], seed=0, dt=1e-3, steps=0, M=8, prec=B.MG_FP64)
+    assert gs["edge"][0] == 1 and gs["x"][0] == 0.25 and gc["particle_steps"] == 0
+    o = oracle_pool.run(d, [1], [0.25], seed=0, dt=1e-3, steps=57, M=8)
+    gs, gc, _ = gpu_run(B, d, [1], [0.25], seed=0, dt=1e-3, steps=57, M=8, prec=B.MG_FP64)
+    assert_fp64_parity(gs, gc, o)
+    # M = 1 with steps far larger than the edges: truncation on nearly every step
+    e, x = W.round_robin_uniform(d, 999, 1)
+    o = oracle_pool.run(d, e, x, seed=2, dt=0.5, steps=40, M=1)
+    gs, gc, _ = gpu_run(B, d, e, x, seed=2, dt=0.5, steps=40, M=1, prec=B.MG_FP64)
+    assert_fp64_parity(gs, gc, o)
+    assert gc["truncations"] > 999 * 10
+    # every particle absorbed
+    da = dict(d, kind=np.array([0, 1, 1, 1], np.uint8))
+    o = oracle_pool.run(da, e, x, seed=2, dt=0.05, steps=400, M=32)
+    gs, gc, _ = gpu_run(B, da, e, x, seed=2, dt=0.05, steps=400, M=32, prec=B.MG_FP64, bins=4)
+    assert_fp64_parity(gs, gc, o)
+    assert np.all(gs["edge"] == -1) and gc["absorbed"].sum() == 999
+
+
+# ------------------------------------------------------------ invariances
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_chunking_sharding_resume_bit_exact(B, prec):
+    P = B.MG_FP64 if prec == "fp64" else B.MG_FP32_MIXED
+    d = W.random_mixed(3)
+    n = 6000
+    e, x = W.uniform_on_edges(d, n, 4)
+    kw = dict(seed=77, dt=3e-3, M=6, prec=P)
+    a, ca, ha = gpu_run(B, d, e, x, steps=600, bins=8, **kw)
+    b, cb, hb = gpu_run(B, d, e, x, steps=600, chunks=[200, 200, 200], bins=8, **kw)
+    c, cc, hc = gpu_run(B, d, e, x, steps=600, chunks=[1, 598, 1], bins=8, **kw)
+    for other, co, ho in [(b, cb, hb), (c, cc, hc)]:
+        for k in ("edge", "x", "hits", "first_hits", "flags"):
+            assert np.array_equal(a[k], other[k]), k
+        for k in ("exits", "absorbed"):
+            assert np.array_equal(ca[k], co[k])
+        assert ca["truncations"] == co["truncations"]
+        assert ca["particle_steps"] == co["particle_steps"]
+        assert np.array_equal(ha, ho)
+    # two shards by particle id sum to the whole
+    s1, c1, h1 = gpu_run(B, d, e[:2500], x[:2500], steps=600, bins=8, **kw)
+    s2, c2, h2 = gpu_run(B, d, e[2500:], x[2500:], steps=600, pid_base=2500, bins=8, **kw)
+    assert np.array_equal(a["x"], np.concatenate([s1["x"], s2["x"]]))
+    assert np.array_equal(ca["exits"], c1["exits"] + c2["exits"])
+    assert np.array_equal(ha, h1 + h2)
+    # checkpoint after 250 steps, resume in a fresh set
+    g = B.Graph(d)
+    p = B.Particles(g, e, x, seed=77, precision=P)
+    p.simulate(3e-3, 250, 6)
+    ck = p.state()
+    q = B.Particles(g, e, x, seed=77, precision=P)
+    q.set_state(ck)
+    q.simulate(3e-3, 350, 6)
+    r = q.state()
+    assert r["step"] == 600
+    for k in ("edge", "x", "hits", "first_hits", "flags"):
+        assert np.array_equal(a[k], r[k]), k
+    p.close(); q.close(); g.close()
+
+
+def test_fused_histogram_matches_standalone(B):
+    import torch
+    d = W.star_langevin(16)
+    e, x = W.uniform_on_edges(d, 50_000, 1)
+    for P in (B.MG_FP32_MIXED, B.MG_FP64):
+        g = B.Graph(d)
+        p = B.Particles(g, e, x, seed=4, precision=P)
+        h = torch.zeros(16 * 32, dtype=torch.int32, device="cuda")
+        p.simulate(1e-3, 500, 16, hist_bins=32, hist_out=h)
+        p.synchronize()
+        alone = p.histogram(32)
+        assert np.array_equal(h.cpu().numpy().view(np.uint32), alone)
+        assert alone.sum() == 50_000
+        p.close(); g.close()
+
+
+def test_device_inputs_and_validation(B):
+    import torch
+    d = W.random_tree(50, seed=1)
+    e, x = W.uniform_on_edges(d, 3000, 5)
+    a, ca, _ = gpu_run(B, d, e, x, seed=3, dt=2e-3, steps=100, M=8, prec=B.MG_FP64)
+    g = B.Graph(d)
+    et = torch.from_numpy(e).cuda()
+    xt = torch.from_numpy(x).cuda()
+    p = B.Particles(g, et, xt, seed=3, precision=B.MG_FP64)
+    p.simulate(2e-3, 100, 8)
+    p.synchronize()
+    s = p.state()
+    assert np.array_equal(s["x"], a["x"]) and np.array_equal(s["edge"], a["edge"])
+    p.close()
+    # an out-of-range edge in device input is reported, not trapped
+    bad = et.clone()
+    bad[17] = 10_000
+    p = B.Particles(g, bad, xt, seed=3, precision=B.MG_FP64)
+    with pytest.raises(B.MGError) as ei:
+        p.synchronize()
+    assert ei.value.status == B.MG_ERR_DEVICE_FAULT
+    p.close()
+    # host input is validated on the host
+    with pytest.raises(B.MGError) as ei:
+        B.Particles(g, np.array([0, 99], np.int32), np.array([0.1, 0.1]), seed=3)
+    assert ei.value.status == B.MG_ERR_INVALID_ARG
+    g.close()
+
+
+def test_torch_allocator_same_results(B):
+    d = W.star_brownian(3)
+    e, x = W.round_robin_uniform(d, 2000, 3)
+    a, ca, _ = gpu_run(B, d, e, x, seed=1, dt=1e-3, steps=300, M=8, prec=B.MG_FP32_MIXED)
+    B.use_torch_allocator()
+    try:
+        b, cb, _ = gpu_run(B, d, e, x, seed=1, dt=1e-3, steps=300, M=8, prec=B.MG_FP32_MIXED)
+    finally:
+        B.use_cuda_allocator()
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(ca["exits"], cb["exits"])
+
+
+# ------------------------------------------------------ FP32-mixed parity
+
+def _occupancy(edge, E):
+    alive = edge >= 0
+    return np.bincount(edge[alive], minlength=E) / len(edge)
+
+
+def test_star16_langevin_fp32_statistics(B):
+    """FP32-mixed vs the FP64 oracle on the 16-edge Langevin star: same
+    streams, N = 2^16, 2000 steps."""
+    d = W.star_langevin(16)
+    n = 1 << 16
+    e, x = W.uniform_on_edges(d, n, 11)
+    gs, gc, gh = gpu_run(B, d, e, x, seed=0, dt=1e-3, steps=2000, M=16, prec=B.MG_FP32_MIXED,
+                         bins=32)
+    o = oracle_pool.run(d, e, x, seed=0, dt=1e-3, steps=2000, M=16, bins=32)
+    po, pg = _occupancy(o["edge"], 16), _occupancy(gs["edge"], 16)
+    se = np.sqrt(po * (1 - po) / n)
+    assert np.all(np.abs(pg - po) <= 3 * se + 1e-12), (pg - po) / se
+    eo = o["exits"].astype(float)
+    eg = gc["exits"].astype(float)
+    fo, fg = eo / eo.sum(), eg / eg.sum()
+    assert np.all(np.abs(fg - fo) <= 3 * np.sqrt(fo * (1 - fo) / eo.sum()) + 1e-12)
+    # coupled streams: almost every particle ends on the same edge, nearby
+    same = gs["edge"] == o["edge"]
+    assert same.mean() > 0.95
+    assert np.median(np.abs(gs["x"][same] - o["x"][same])) < 1e-4
+    tv = 0.5 * np.abs(gh / n - o["hist"] / n).sum()
+    assert tv < 0.02, tv
+
+
+def test_star16_full_size_sampled(B):
+    """The benchmark's configuration (N = 2^24, 10^4 steps, M = 16, FP32-mixed)
+    against oracle trajectories of 1024 sampled particles, plus FP64 mode at
+    full N on 200 steps, trajectory by trajectory on the same sample."""
+    import torch
+    d = W.star_langevin(16)
+    n = 1 << 24
+    e, x = W.uniform_on_edges(d, n, 11)
+    idx = np.sort(np.random.default_rng(5).choice(n, 1024, replace=False))
+    h = torch.zeros(16 * 32, dtype=torch.int32, device="cuda")
+    g = B.Graph(d)
+    p = B.Particles(g, e, x, seed=0, precision=B.MG_FP32_MIXED)
+    p.simulate(1e-3, 10_000, 16, hist_bins=32, hist_out=h)
+    p.synchronize()
+    st = p.state()
+    cnt = p.counts()
+    p.close()
+    hist = h.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert hist.sum() == n and cnt["particle_steps"] == n * 10_000
+    o = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=1e-3, steps=10_000, M=16)
+    same = st["edge"][idx] == o["edge"]
+    assert same.mean() > 0.85, same.mean()
+    po = _occupancy(o["edge"], 16)
+    pg = np.bincount(st["edge"], minlength=16) / n
+    assert np.all(np.abs(pg - po) <= 3 * np.sqrt(po * (1 - po) / len(idx)) + 1e-9)
+    # FP64 at full N: sampled trajectories exact
+    p = B.Particles(g, e, x, seed=0, precision=B.MG_FP64)
+    p.simulate(1e-3, 200, 16)
+    p.synchronize()
+    s64 = p.state()
+    p.close()
+    g.close()
+    o64 = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=1e-3, steps=200, M=16)
+    sub = {k: s64[k][idx] for k in ("edge", "x", "hits", "first_hits", "flags")}
+    flagged = ((sub["flags"] | o64["flags"]) & 1) != 0
+    ok = ~flagged
+    assert np.array_equal(sub["edge"][ok], o64["edge"][ok])
+    assert np.all(np.abs(sub["x"][ok] - o64["x"][ok]) <= REL * np.maximum(1, np.abs(o64["x"][ok])))
+
+
+def test_star16_coupled_tv_fp32_vs_fp64_full_n(B):
+    """Coupled total-variation distance between the FP32-mixed and FP64
+    histograms at N = 2^24 (both GPU; the FP64 mode is the oracle's
+    trajectories, as the tests above show).  Two independent histograms of
+    N particles over 512 bins would differ by about sqrt(512 / (pi N)) =
+    3.1e-3; shared random streams bring the coupled distance under 1e-3."""
+    import torch
+    d = W.star_langevin(16)
+    n = 1 << 24
+    e, x = W.uniform_on_edges(d, n, 11)
+    hs = []
+    g = B.Graph(d)
+    for P in (B.MG_FP32_MIXED, B.MG_FP64):
+        h = torch.zeros(16 * 32, dtype=torch.int32, device="cuda")
+        p = B.Particles(g, e, x, seed=0, precision=P)
+        p.simulate(1e-3, 1000, 16, hist_bins=32, hist_out=h)
+        p.synchronize()
+        hs.append(h.cpu().numpy().view(np.uint32).astype(np.int64))
+        p.close()
+    g.close()
+    tv = 0.5 * np.abs(hs[0] - hs[1]).sum() / n
+    assert tv <= 1e-3, tv
