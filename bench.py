@@ -119,7 +119,7 @@ def _oracle_chunk(args):
     g = O.Graph.from_desc(desc)
     st = O.State(edge, x, pid)
     cnt = O.Counters(g)
-    O.simulate(g, st, cnt, seed=SEED, instance=0, t0=0, dt=DT, steps=steps, M=M)
+    O.simulate(g, st, cnt, seed=SEED, instance=0, dt=DT, steps=steps, M=M)
     return int(cnt.particle_steps[0])
 
 

@@ -90,16 +90,16 @@ static void key_of_seed(uint64_t seed, uint32_t key[2]) {
   key[1] = (uint32_t)(seed >> 32);
 }
 
-double or_main_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint64_t t) {
+double or_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t n) {
   uint32_t key[2], ctr[4], w[4];
   key_of_seed(seed, key);
-  ctr[0] = (uint32_t)(t >> 2);
+  ctr[0] = n >> 2;
   ctr[1] = pid;
-  ctr[2] = 0u; /* tag 0: normals of the main sub-steps */
+  ctr[2] = 0u; /* tag 0: normals of the sub-steps */
   ctr[3] = instance;
   or_philox4x32_10(ctr, key, w);
   double zc, zs;
-  switch ((int)(t & 3u)) {
+  switch ((int)(n & 3u)) {
     case 0: or_box_muller(w[0], w[1], &zc, &zs); return zc;
     case 1: or_box_muller(w[0], w[1], &zc, &zs); return zs;
     case 2: or_box_muller(w[2], w[3], &zc, &zs); return zc;
@@ -107,8 +107,7 @@ double or_main_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint64_t t
   }
 }
 
-void or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j,
-                   uint32_t* u, double* z) {
+uint32_t or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j) {
   uint32_t key[2], ctr[4], w[4];
   key_of_seed(seed, key);
   ctr[0] = j;
@@ -116,10 +115,7 @@ void or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j,
   ctr[2] = 1u; /* tag 1: draws of vertex hits */
   ctr[3] = instance;
   or_philox4x32_10(ctr, key, w);
-  double zc, zs;
-  or_box_muller(w[2], w[3], &zc, &zs);
-  *u = w[0];
-  *z = zc;
+  return w[0];
 }
 
 /* ------------------------------------------------------------------- graph */
@@ -285,27 +281,29 @@ double or_root(double A, double B, double C) {
 
 /* ------------------------------------------------------------------ EM-Step */
 
-static void philox_split_draw(or_split_source* self, const or_particle* p, uint32_t j,
-                              uint32_t* u, double* z) {
+static double philox_normal(or_draws* self, or_particle* p) {
+  double z = or_normal(self->seed, self->instance, self->pid, p->n_draw);
+  p->n_draw++;
+  return z;
+}
+
+static uint32_t philox_split(or_draws* self, const or_particle* p, uint32_t j) {
   (void)p;
-  or_split_draw(self->seed, self->instance, self->pid, j, u, z);
+  return or_split_draw(self->seed, self->instance, self->pid, j);
 }
 
-static void injected_split_draw(or_split_source* self, const or_particle* p, uint32_t j,
-                                uint32_t* u, double* z) {
+static double injected_normal(or_draws* self, or_particle* p) {
+  p->n_draw++;
+  return (self->pos_z < self->n_z) ? self->zs[self->pos_z++] : 0.0;
+}
+
+static uint32_t injected_split(or_draws* self, const or_particle* p, uint32_t j) {
   (void)p; (void)j;
-  if (self->pos < self->n_inj) {
-    *u = self->us[self->pos];
-    *z = self->zs[self->pos];
-  } else {
-    *u = 0u;
-    *z = 0.0;
-  }
-  self->pos++;
+  return (self->pos_u < self->n_u) ? self->us[self->pos_u++] : 0u;
 }
 
-int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, double W,
-               or_split_source* src, or_counters* cnt) {
+int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, or_draws* rnd,
+               or_counters* cnt) {
   if (p->edge == OR_DEAD) return 0;
   double h = dt; /* time left in this step */
   int32_t k = 0; /* splits taken in this step */
@@ -317,6 +315,7 @@ int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, double W
     int at_end = -1;
     if (p->x == 0.0) at_end = OR_END_INIT;
     else if (p->x == l) at_end = OR_END_TERM;
+    double W = rnd->normal(rnd, p);               /* Sample W ~ N(0,1) */
     if (at_end == OR_END_INIT) W = fabs(W);       /* R1 */
     else if (at_end == OR_END_TERM) W = -fabs(W); /* R1 */
 
@@ -358,9 +357,7 @@ int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, double W
     }
 
     /* sample the next edge from b_v (R4) and restart at its end */
-    uint32_t u;
-    double z;
-    src->draw(src, p, j, &u, &z);
+    uint32_t u = rnd->split(rnd, p, j);
     int32_t slot = or_choose_slot(g, v, u);
     int32_t e2 = g->slot_edge[slot];
     p->edge = e2;
@@ -371,13 +368,13 @@ int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, double W
       return k;
     }
     if (h <= 0.0) return k;
-    W = z; /* a fresh normal for the rest of the step */
+    /* the rest of the step continues from the vertex with the next normal */
   }
 }
 
 void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edge,
-                 double* x, uint32_t* hits, uint32_t* first_hits, uint32_t* flags,
-                 uint64_t seed, uint32_t instance, uint64_t t0, double dt,
+                 double* x, uint32_t* n_draw, uint32_t* hits, uint32_t* first_hits,
+                 uint32_t* flags, uint64_t seed, uint32_t instance, double dt,
                  int64_t steps, int32_t M, uint64_t* exits, uint64_t* absorbed,
                  uint64_t* truncations, int64_t* particle_steps) {
   or_counters cnt;
@@ -387,20 +384,19 @@ void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edg
   int64_t ps = 0;
   for (int64_t i = 0; i < n; ++i) {
     or_particle p;
-    p.edge = edge[i]; p.x = x[i]; p.hits = hits[i];
+    p.edge = edge[i]; p.x = x[i]; p.n_draw = n_draw[i]; p.hits = hits[i];
     p.first_hits = first_hits[i]; p.flags = flags[i];
-    or_split_source src;
-    memset(&src, 0, sizeof src);
-    src.draw = philox_split_draw;
-    src.seed = seed; src.instance = instance; src.pid = pid[i];
+    or_draws rnd;
+    memset(&rnd, 0, sizeof rnd);
+    rnd.normal = philox_normal;
+    rnd.split = philox_split;
+    rnd.seed = seed; rnd.instance = instance; rnd.pid = pid[i];
     for (int64_t st = 0; st < steps; ++st) {
       if (p.edge == OR_DEAD) break;
-      uint64_t t = t0 + (uint64_t)st;
-      double W = or_main_normal(seed, instance, pid[i], t);
-      or_em_step(g, &p, dt, M, W, &src, &cnt);
+      or_em_step(g, &p, dt, M, &rnd, &cnt);
       ps++;
     }
-    edge[i] = p.edge; x[i] = p.x; hits[i] = p.hits;
+    edge[i] = p.edge; x[i] = p.x; n_draw[i] = p.n_draw; hits[i] = p.hits;
     first_hits[i] = p.first_hits; flags[i] = p.flags;
   }
   *truncations += cnt.truncations;
@@ -419,20 +415,24 @@ void or_histogram(const or_graph* g, int64_t n, const int32_t* edge, const doubl
   }
 }
 
-int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* hits,
-                        uint32_t* first_hits, uint32_t* flags, double dt, int32_t M,
-                        double W, const uint32_t* us, const double* zs, int32_t n_inj,
-                        uint64_t* exits, uint64_t* absorbed, uint64_t* truncations) {
+int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* n_draw,
+                        uint32_t* hits, uint32_t* first_hits, uint32_t* flags, double dt,
+                        int32_t M, const double* zs, int32_t n_z, const uint32_t* us,
+                        int32_t n_u, uint64_t* exits, uint64_t* absorbed,
+                        uint64_t* truncations) {
   or_particle p;
-  p.edge = *edge; p.x = *x; p.hits = *hits; p.first_hits = *first_hits; p.flags = *flags;
-  or_split_source src;
-  memset(&src, 0, sizeof src);
-  src.draw = injected_split_draw;
-  src.us = us; src.zs = zs; src.n_inj = n_inj; src.pos = 0;
+  p.edge = *edge; p.x = *x; p.n_draw = *n_draw; p.hits = *hits; p.first_hits = *first_hits;
+  p.flags = *flags;
+  or_draws rnd;
+  memset(&rnd, 0, sizeof rnd);
+  rnd.normal = injected_normal;
+  rnd.split = injected_split;
+  rnd.zs = zs; rnd.n_z = n_z; rnd.us = us; rnd.n_u = n_u;
   or_counters cnt;
   cnt.exits = exits; cnt.absorbed = absorbed; cnt.truncations = 0;
-  int k = or_em_step(g, &p, dt, M, W, &src, &cnt);
-  *edge = p.edge; *x = p.x; *hits = p.hits; *first_hits = p.first_hits; *flags = p.flags;
+  int k = or_em_step(g, &p, dt, M, &rnd, &cnt);
+  *edge = p.edge; *x = p.x; *n_draw = p.n_draw; *hits = p.hits; *first_hits = p.first_hits;
+  *flags = p.flags;
   *truncations += cnt.truncations;
   return k;
 }

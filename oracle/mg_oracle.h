@@ -35,15 +35,14 @@ double or_u01(uint32_t w);
  * z_cos = r cos(theta), z_sin = r sin(theta). */
 void or_box_muller(uint32_t wa, uint32_t wb, double* z_cos, double* z_sin);
 
-/* Normal used by the main (first) sub-step of EM step t of particle pid:
- * block (t>>2, pid, 0, instance) under key (seed lo, seed hi); lane t&3
- * picks z_cos(w0,w1), z_sin(w0,w1), z_cos(w2,w3), z_sin(w2,w3). */
-double or_main_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint64_t t);
+/* The n-th normal of particle pid (one per Euler-Maruyama sub-step, in
+ * order): block (n>>2, pid, 0, instance) under key (seed lo, seed hi); lane
+ * n&3 picks z_cos(w0,w1), z_sin(w0,w1), z_cos(w2,w3), z_sin(w2,w3). */
+double or_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t n);
 
-/* Draws of the j-th vertex hit of particle pid: block (j, pid, 1, instance);
- * *u = w0 (edge choice), *z = z_cos(w2, w3) (normal of the next sub-step). */
-void or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j,
-                   uint32_t* u, double* z);
+/* The uniform 32-bit draw of the j-th vertex hit of particle pid (it picks
+ * the next edge): word w0 of block (j, pid, 1, instance). */
+uint32_t or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j);
 
 /* ----------------------------------------------------------------- graph */
 
@@ -97,6 +96,7 @@ double or_root(double A, double B, double C);
 typedef struct {
   int32_t edge;        /* OR_DEAD once absorbed */
   double x;            /* position on the edge, measured from e_init */
+  uint32_t n_draw;     /* normals used so far (= index of the next one) */
   uint32_t hits;       /* vertex hits so far (= index of the next split draw) */
   uint32_t first_hits; /* hits that started from the interior of an edge */
   uint32_t flags;      /* bit 0: trajectory passed within 1e-9 of a branch */
@@ -110,29 +110,30 @@ typedef struct {
   uint64_t truncations; /* steps that hit the split cap M */
 } or_counters;
 
-/* Source of the draws of the vertex hits (Philox normally; tests inject
- * hand-chosen sequences). */
-typedef struct or_split_source {
-  void (*draw)(struct or_split_source* self, const or_particle* p, uint32_t j,
-               uint32_t* u, double* z);
+/* Source of the random draws (Philox normally; tests inject hand-chosen
+ * sequences): normal() returns the particle's next normal and advances
+ * p->n_draw; split() returns the u32 of the particle's j-th vertex hit. */
+typedef struct or_draws {
+  double (*normal)(struct or_draws* self, or_particle* p);
+  uint32_t (*split)(struct or_draws* self, const or_particle* p, uint32_t j);
   uint64_t seed;
   uint32_t instance, pid;
   /* injection */
-  const uint32_t* us;
   const double* zs;
-  int32_t n_inj, pos;
-} or_split_source;
+  const uint32_t* us;
+  int32_t n_z, n_u, pos_z, pos_u;
+} or_draws;
 
-/* One EM-Step of length dt (Algorithm 2 with the readings of Algorithm 1);
- * W is the normal of the first sub-step.  Returns the number of splits. */
-int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, double W,
-               or_split_source* src, or_counters* cnt);
+/* One EM-Step of length dt (Algorithm 2 with the readings of Algorithm 1).
+ * Returns the number of splits. */
+int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, or_draws* rnd,
+               or_counters* cnt);
 
-/* Advance particles i = 0..n-1 (global ids pid[i]) over steps t0..t0+steps-1.
+/* Advance particles i = 0..n-1 (global ids pid[i]) by `steps` EM-Steps.
  * State arrays are updated in place; counters accumulate. */
 void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edge,
-                 double* x, uint32_t* hits, uint32_t* first_hits, uint32_t* flags,
-                 uint64_t seed, uint32_t instance, uint64_t t0, double dt,
+                 double* x, uint32_t* n_draw, uint32_t* hits, uint32_t* first_hits,
+                 uint32_t* flags, uint64_t seed, uint32_t instance, double dt,
                  int64_t steps, int32_t M, uint64_t* exits, uint64_t* absorbed,
                  uint64_t* truncations, int64_t* particle_steps);
 
@@ -141,11 +142,13 @@ void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edg
 void or_histogram(const or_graph* g, int64_t n, const int32_t* edge, const double* x,
                   int32_t B, uint64_t* hist);
 
-/* Test hook: one EM-Step of one particle with injected draws. */
-int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* hits,
-                        uint32_t* first_hits, uint32_t* flags, double dt, int32_t M,
-                        double W, const uint32_t* us, const double* zs, int32_t n_inj,
-                        uint64_t* exits, uint64_t* absorbed, uint64_t* truncations);
+/* Test hook: one EM-Step of one particle with injected draws: the normals
+ * zs[0..n_z) of its sub-steps in order, the u32s us[0..n_u) of its hits. */
+int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* n_draw,
+                        uint32_t* hits, uint32_t* first_hits, uint32_t* flags, double dt,
+                        int32_t M, const double* zs, int32_t n_z, const uint32_t* us,
+                        int32_t n_u, uint64_t* exits, uint64_t* absorbed,
+                        uint64_t* truncations);
 
 #ifdef __cplusplus
 }

@@ -63,10 +63,10 @@ def _declare(L):
     L.or_u01.restype = dbl
     L.or_box_muller.argtypes = [u32, u32, _p(dbl), _p(dbl)]
     L.or_box_muller.restype = None
-    L.or_main_normal.argtypes = [u64, u32, u32, u64]
-    L.or_main_normal.restype = dbl
-    L.or_split_draw.argtypes = [u64, u32, u32, u32, _p(u32), _p(dbl)]
-    L.or_split_draw.restype = None
+    L.or_normal.argtypes = [u64, u32, u32, u32]
+    L.or_normal.restype = dbl
+    L.or_split_draw.argtypes = [u64, u32, u32, u32]
+    L.or_split_draw.restype = u32
     L.or_graph_build.argtypes = [i32, i32, _p(i32), _p(i32), _p(dbl), _p(dbl), _p(dbl), _p(dbl),
                                  _p(dbl), _p(dbl), _p(dbl), _p(u8), C.POINTER(C.c_void_p)]
     L.or_graph_build.restype = C.c_int
@@ -81,14 +81,14 @@ def _declare(L):
     L.or_root.argtypes = [dbl, dbl, dbl]
     L.or_root.restype = dbl
     L.or_simulate.argtypes = [C.c_void_p, i64, _p(u32), _p(i32), _p(dbl), _p(u32), _p(u32),
-                              _p(u32), u64, u32, u64, dbl, i64, i32, _p(u64), _p(u64), _p(u64),
-                              _p(i64)]
+                              _p(u32), _p(u32), u64, u32, dbl, i64, i32, _p(u64), _p(u64),
+                              _p(u64), _p(i64)]
     L.or_simulate.restype = None
     L.or_histogram.argtypes = [C.c_void_p, i64, _p(i32), _p(dbl), i32, _p(u64)]
     L.or_histogram.restype = None
     L.or_em_step_injected.argtypes = [C.c_void_p, _p(i32), _p(dbl), _p(u32), _p(u32), _p(u32),
-                                      dbl, i32, dbl, _p(u32), _p(dbl), i32, _p(u64), _p(u64),
-                                      _p(u64)]
+                                      _p(u32), dbl, i32, _p(dbl), i32, _p(u32), i32, _p(u64),
+                                      _p(u64), _p(u64)]
     L.or_em_step_injected.restype = C.c_int
 
 
@@ -117,14 +117,14 @@ def box_muller(wa: int, wb: int):
     return zc.value, zs.value
 
 
-def main_normal(seed: int, instance: int, pid: int, t: int) -> float:
-    return lib().or_main_normal(seed, instance, pid, t)
+def normal(seed: int, instance: int, pid: int, n: int) -> float:
+    """The n-th normal of particle pid."""
+    return lib().or_normal(seed, instance, pid, n)
 
 
-def split_draw(seed: int, instance: int, pid: int, j: int):
-    u, z = C.c_uint32(), C.c_double()
-    lib().or_split_draw(seed, instance, pid, j, C.byref(u), C.byref(z))
-    return u.value, z.value
+def split_draw(seed: int, instance: int, pid: int, j: int) -> int:
+    """The u32 of the j-th vertex hit of particle pid."""
+    return lib().or_split_draw(seed, instance, pid, j)
 
 
 def root(A: float, B: float, Cc: float) -> float:
@@ -204,6 +204,7 @@ class State:
         n = len(edge)
         self.edge = np.ascontiguousarray(edge, dtype=np.int32).copy()
         self.x = np.ascontiguousarray(x, dtype=np.float64).copy()
+        self.n_draw = np.zeros(n, np.uint32)
         self.hits = np.zeros(n, np.uint32)
         self.first_hits = np.zeros(n, np.uint32)
         self.flags = np.zeros(n, np.uint32)
@@ -222,16 +223,17 @@ class Counters:
         self.particle_steps = np.zeros(1, np.int64)
 
 
-def simulate(g: Graph, st: State, cnt: Counters, *, seed: int, instance: int, t0: int,
-             dt: float, steps: int, M: int):
-    """Advance every particle of ``st`` by ``steps`` EM-Steps from global step t0."""
+def simulate(g: Graph, st: State, cnt: Counters, *, seed: int, instance: int, dt: float,
+             steps: int, M: int):
+    """Advance every particle of ``st`` by ``steps`` EM-Steps."""
     if not (dt > 0) or M < 1 or steps < 0:
         raise ValueError("oracle: dt > 0, M >= 1, steps >= 0 required")
     n = len(st)
     lib().or_simulate(g._h, n, _ptr(st.pid, C.c_uint32), _ptr(st.edge, C.c_int32),
-                      _ptr(st.x, C.c_double), _ptr(st.hits, C.c_uint32),
-                      _ptr(st.first_hits, C.c_uint32), _ptr(st.flags, C.c_uint32),
-                      int(seed), int(instance), int(t0), float(dt), int(steps), int(M),
+                      _ptr(st.x, C.c_double), _ptr(st.n_draw, C.c_uint32),
+                      _ptr(st.hits, C.c_uint32), _ptr(st.first_hits, C.c_uint32),
+                      _ptr(st.flags, C.c_uint32), int(seed), int(instance), float(dt),
+                      int(steps), int(M),
                       _ptr(cnt.exits, C.c_uint64), _ptr(cnt.absorbed, C.c_uint64),
                       _ptr(cnt.truncations, C.c_uint64), _ptr(cnt.particle_steps, C.c_int64))
 
@@ -243,22 +245,25 @@ def histogram(g: Graph, st: State, bins: int) -> np.ndarray:
     return h
 
 
-def em_step_injected(g: Graph, edge: int, x: float, dt: float, M: int, W: float, us, zs,
-                     hits: int = 0, first_hits: int = 0, flags: int = 0):
-    """One EM-Step of one particle with the normal W of the first sub-step and
-    the hit draws (u_k, z_k) injected.  Returns (edge, x, hits, first_hits,
-    flags, splits, exits, absorbed, truncations)."""
+def em_step_injected(g: Graph, edge: int, x: float, dt: float, M: int, zs, us,
+                     n_draw: int = 0, hits: int = 0, first_hits: int = 0, flags: int = 0):
+    """One EM-Step of one particle with its draws injected: ``zs`` the normals
+    of its sub-steps in order, ``us`` the u32s of its vertex hits.  Returns
+    (edge, x, n_draw, hits, first_hits, flags, splits, exits, absorbed,
+    truncations) as a dict."""
     e_, x_ = C.c_int32(edge), C.c_double(x)
-    h_, f_, fl_ = C.c_uint32(hits), C.c_uint32(first_hits), C.c_uint32(flags)
-    us = np.ascontiguousarray(us if len(us) else [0], dtype=np.uint32)
-    zs = np.ascontiguousarray(zs if len(zs) else [0.0], dtype=np.float64)
+    nd_, h_ = C.c_uint32(n_draw), C.c_uint32(hits)
+    f_, fl_ = C.c_uint32(first_hits), C.c_uint32(flags)
+    zs = np.ascontiguousarray(list(zs) if len(zs) else [0.0], dtype=np.float64)
+    us = np.ascontiguousarray(list(us) if len(us) else [0], dtype=np.uint32)
     exits = np.zeros(g.n_slots, np.uint64)
     absorbed = np.zeros(g.n_vertices, np.uint64)
     tr = np.zeros(1, np.uint64)
-    k = lib().or_em_step_injected(g._h, C.byref(e_), C.byref(x_), C.byref(h_), C.byref(f_),
-                                  C.byref(fl_), float(dt), int(M), float(W),
-                                  _ptr(us, C.c_uint32), _ptr(zs, C.c_double), len(us),
+    k = lib().or_em_step_injected(g._h, C.byref(e_), C.byref(x_), C.byref(nd_), C.byref(h_),
+                                  C.byref(f_), C.byref(fl_), float(dt), int(M),
+                                  _ptr(zs, C.c_double), len(zs), _ptr(us, C.c_uint32), len(us),
                                   _ptr(exits, C.c_uint64), _ptr(absorbed, C.c_uint64),
                                   _ptr(tr, C.c_uint64))
-    return dict(edge=e_.value, x=x_.value, hits=h_.value, first_hits=f_.value, flags=fl_.value,
-                splits=k, exits=exits, absorbed=absorbed, truncations=int(tr[0]))
+    return dict(edge=e_.value, x=x_.value, n_draw=nd_.value, hits=h_.value,
+                first_hits=f_.value, flags=fl_.value, splits=k, exits=exits,
+                absorbed=absorbed, truncations=int(tr[0]))

@@ -15,15 +15,15 @@ _POOL = None
 
 
 def _worker(args):
-    desc, edge, x, pid, seed, instance, t0, dt, steps, M, bins = args
+    desc, edge, x, pid, seed, instance, dt, steps, M, bins = args
     from oracle import oracle as O
     g = O.Graph.from_desc(desc)
     st = O.State(edge, x, pid)
     cnt = O.Counters(g)
-    O.simulate(g, st, cnt, seed=seed, instance=instance, t0=t0, dt=dt, steps=steps, M=M)
+    O.simulate(g, st, cnt, seed=seed, instance=instance, dt=dt, steps=steps, M=M)
     hist = O.histogram(g, st, bins) if bins else None
     return (st.edge, st.x, st.hits, st.first_hits, st.flags, cnt.exits, cnt.absorbed,
-            int(cnt.truncations[0]), int(cnt.particle_steps[0]), hist)
+            int(cnt.truncations[0]), int(cnt.particle_steps[0]), hist, st.n_draw)
 
 
 def _pool():
@@ -34,7 +34,7 @@ def _pool():
     return _POOL
 
 
-def run(desc, edge, x, pid=None, *, seed, instance=0, t0=0, dt, steps, M, bins=0, chunks=None):
+def run(desc, edge, x, pid=None, *, seed, instance=0, dt, steps, M, bins=0, chunks=None):
     """Oracle over all particles; returns a dict of state, counters, histogram."""
     from oracle import oracle as O
     O.build()  # once here, not racing in every worker
@@ -49,7 +49,7 @@ def run(desc, edge, x, pid=None, *, seed, instance=0, t0=0, dt, steps, M, bins=0
     if chunks is None:
         chunks = 1 if work < 2_000_000 else min(64, max(2, work // 2_000_000))
     bounds = np.linspace(0, n, chunks + 1).astype(np.int64)
-    jobs = [(desc, edge[a:b], x[a:b], pid[a:b], seed, instance, t0, dt, steps, M, bins)
+    jobs = [(desc, edge[a:b], x[a:b], pid[a:b], seed, instance, dt, steps, M, bins)
             for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
     res = [_worker(jobs[0])] if len(jobs) == 1 else _pool().map(_worker, jobs)
     cat = lambda k: np.concatenate([r[k] for r in res])
@@ -57,4 +57,5 @@ def run(desc, edge, x, pid=None, *, seed, instance=0, t0=0, dt, steps, M, bins=0
                exits=sum(r[5] for r in res), absorbed=sum(r[6] for r in res),
                truncations=sum(r[7] for r in res), particle_steps=sum(r[8] for r in res))
     out["hist"] = sum(r[9] for r in res) if bins else None
+    out["n_draw"] = cat(10)
     return out

@@ -33,7 +33,7 @@ def _sim(oracle, d, edge, x, seed, dt, steps, M):
     g = oracle.Graph.from_desc(d)
     st = oracle.State(edge, x)
     cnt = oracle.Counters(g)
-    oracle.simulate(g, st, cnt, seed=seed, instance=0, t0=0, dt=dt, steps=steps, M=M)
+    oracle.simulate(g, st, cnt, seed=seed, instance=0, dt=dt, steps=steps, M=M)
     return g, st, cnt
 
 

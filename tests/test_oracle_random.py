@@ -6,7 +6,7 @@
 * Box-Muller: the normals pass a Kolmogorov-Smirnov test against scipy's
   normal CDF; r^2 is exponential with mean 2 (a dropped factor 2 in
   -2 ln u fails); the angle is uniform; cos/sin partners are uncorrelated.
-* The split draws: u32 uniform (chi-square over 256 cells), z normal.
+* The split draws: every byte of the u32 uniform (chi-square over 256 cells).
 """
 import os
 import subprocess
@@ -79,7 +79,7 @@ def _many_normals(oracle, n_pid=64, n_t=2048, seed=5, instance=2):
     i = 0
     for pid in range(n_pid):
         for t in range(n_t):
-            z[i] = oracle.main_normal(seed, instance, pid, t)
+            z[i] = oracle.normal(seed, instance, pid, t)
             i += 1
     return z.reshape(n_pid, n_t)
 
@@ -104,24 +104,18 @@ def test_main_normals_are_standard_normal(oracle):
 
 
 def test_split_draws(oracle):
-    us, zs = [], []
-    for pid in range(32):
-        for j in range(1024):
-            u, zz = oracle.split_draw(9, 1, pid, j)
-            us.append(u)
-            zs.append(zz)
-    us = np.array(us, dtype=np.uint64)
-    counts = np.bincount((us >> 24).astype(np.int64), minlength=256)
-    assert stats.chisquare(counts).pvalue > 1e-3
-    assert stats.kstest(np.array(zs), "norm").pvalue > 1e-3
+    us = np.array([oracle.split_draw(9, 1, pid, j) for pid in range(32) for j in range(1024)],
+                  dtype=np.uint64)
+    for shift in (0, 8, 16, 24):  # every byte of the word is uniform (4 tests: 1e-4 each)
+        counts = np.bincount(((us >> shift) & 255).astype(np.int64), minlength=256)
+        assert stats.chisquare(counts).pvalue > 1e-4
 
 
 def test_streams_are_distinct(oracle):
     # tag, pid, instance and seed each change the stream
-    a = oracle.main_normal(1, 0, 0, 0)
-    assert a != oracle.main_normal(2, 0, 0, 0)
-    assert a != oracle.main_normal(1, 1, 0, 0)
-    assert a != oracle.main_normal(1, 0, 1, 0)
-    assert a != oracle.main_normal(1, 0, 0, 4)
-    u, z = oracle.split_draw(1, 0, 0, 0)
-    assert z != a
+    a = oracle.normal(1, 0, 0, 0)
+    assert a != oracle.normal(2, 0, 0, 0)
+    assert a != oracle.normal(1, 1, 0, 0)
+    assert a != oracle.normal(1, 0, 1, 0)
+    assert a != oracle.normal(1, 0, 0, 4)
+    assert oracle.split_draw(1, 0, 0, 0) != oracle.split_draw(1, 0, 0, 1)

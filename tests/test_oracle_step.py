@@ -25,7 +25,7 @@ def _star(oracle, lengths=(1.0, 0.5, 2.0), c0=0.0, c1=0.0, sigma=1.0, w=None, ki
 
 def test_interior_step(oracle):
     g = _star(oracle)
-    r = oracle.em_step_injected(g, 0, 0.5, 0.01, 8, 1.0, [], [])
+    r = oracle.em_step_injected(g, 0, 0.5, 0.01, 8, [1.0], [])
     assert r["edge"] == 0 and r["x"] == 0.5 + math.sqrt(0.01)
     assert r["splits"] == 0 and r["hits"] == 0 and r["exits"].sum() == 0
 
@@ -36,7 +36,7 @@ def test_hit_centre_brownian(oracle):
     T0 = int(T[0])
     # x = 0.05, W = -1, h = 0.01: x~ = -0.05 -> alpha = 0.05^2/(0.01*1) = 0.25 -> h' = 0.0075
     for u, e_new in [(0, 0), (T0 - 1, 0), (T0, 1), (TWO32 - 1, 2)]:
-        r = oracle.em_step_injected(g, 0, 0.05, 0.01, 8, -1.0, [u], [-0.3])
+        r = oracle.em_step_injected(g, 0, 0.05, 0.01, 8, [-1.0, -0.3], [u])
         assert r["edge"] == e_new
         # from the vertex the rest of the step goes into the edge with |z|
         assert abs(r["x"] - 0.3 * math.sqrt(0.0075)) < 1e-15
@@ -47,7 +47,7 @@ def test_hit_centre_brownian(oracle):
 def test_hit_leaf_reflects(oracle):
     g = _star(oracle)
     # edge 0 has length 1; x = 0.95, W = +1, h = 0.01: leaf hit at alpha = 0.25
-    r = oracle.em_step_injected(g, 0, 0.95, 0.01, 8, 1.0, [12345], [0.7])
+    r = oracle.em_step_injected(g, 0, 0.95, 0.01, 8, [1.0, 0.7], [12345])
     assert r["edge"] == 0
     assert abs(r["x"] - (1.0 - 0.7 * math.sqrt(0.0075))) < 1e-15
     off, se, send, T = g.slots()
@@ -58,7 +58,7 @@ def test_hit_leaf_reflects(oracle):
 def test_drift_hit_init_end(oracle):
     # mu = -0.4, h = 0.25, x = 0.1, W = -0.3: 0.1 - 0.1 s^2 - 0.15 s = 0 at s = 1/2
     g = _star(oracle, lengths=(1.0, 1.0), c0=-0.4)
-    r = oracle.em_step_injected(g, 0, 0.1, 0.25, 8, -0.3, [0], [1.0])
+    r = oracle.em_step_injected(g, 0, 0.1, 0.25, 8, [-0.3, 1.0], [0])
     h2 = 0.25 * 0.75
     assert r["edge"] == 0
     assert abs(r["x"] - (-0.4 * h2 + math.sqrt(h2) * 1.0)) < 1e-14
@@ -70,7 +70,7 @@ def test_drift_hit_term_end_sign(oracle):
     # (1 - 0.9) - 0.1 s^2 - 0.15 s = 0 at s = 1/2, alpha = 1/4.
     # (Solving with the unnegated increment has no root in (0,1].)
     g = _star(oracle, lengths=(1.0, 1.0), c0=0.4)
-    r = oracle.em_step_injected(g, 0, 0.9, 0.25, 8, 0.3, [0], [1.0])
+    r = oracle.em_step_injected(g, 0, 0.9, 0.25, 8, [0.3, 1.0], [0])
     h2 = 0.25 * 0.75
     assert r["edge"] == 0  # leaf: back onto edge 0 at its term end
     # from the term end into the edge: x = L + mu h2 - sqrt(h2) |z|
@@ -82,7 +82,7 @@ def test_return_to_vertex_then_exit(oracle):
     # x~ = -0.05 + 0.03 < 0 -> alpha = 0.09/(25*0.01) = 0.36 (Algorithm 1)
     g = _star(oracle, lengths=(1.0, 1.0), c0=-5.0)
     off, se, send, T = g.slots()
-    r = oracle.em_step_injected(g, 0, 0.0, 0.01, 8, -0.3, [int(T[0])], [2.0])
+    r = oracle.em_step_injected(g, 0, 0.0, 0.01, 8, [-0.3, 2.0], [int(T[0])])
     h2 = 0.01 * (1 - 0.36)
     assert r["edge"] == 1
     assert abs(r["x"] - (-5.0 * h2 + math.sqrt(h2) * 2.0)) < 1e-14
@@ -93,7 +93,7 @@ def test_truncation_at_M(oracle):
     g = _star(oracle, lengths=(1.0, 1.0), c0=-5.0)
     off, se, send, T = g.slots()
     # M = 2: two returns to the vertex -> stop there on the second chosen edge
-    r = oracle.em_step_injected(g, 0, 0.0, 0.01, 2, 0.3, [0, int(T[0])], [0.1, 0.1])
+    r = oracle.em_step_injected(g, 0, 0.0, 0.01, 2, [0.3, 0.1], [0, int(T[0])])
     assert r["splits"] == 2 and r["truncations"] == 1
     assert r["edge"] == 1 and r["x"] == 0.0
     assert r["exits"].sum() == 0
@@ -101,16 +101,16 @@ def test_truncation_at_M(oracle):
 
 def test_absorbing_vertex(oracle):
     g = _star(oracle, lengths=(1.0, 1.0), kind=[0, 1, 0])
-    r = oracle.em_step_injected(g, 0, 0.99, 0.01, 8, 1.0, [0], [0.0])
+    r = oracle.em_step_injected(g, 0, 0.99, 0.01, 8, [1.0], [0])
     assert r["edge"] == -1 and r["absorbed"][1] == 1 and r["hits"] == 1
     # a dead particle does not move
-    r2 = oracle.em_step_injected(g, -1, 0.5, 0.01, 8, 1.0, [0], [0.0])
+    r2 = oracle.em_step_injected(g, -1, 0.5, 0.01, 8, [1.0], [0])
     assert r2["edge"] == -1 and r2["x"] == 0.5 and r2["splits"] == 0
 
 
 def test_semi_infinite_edge_never_hits_far_end(oracle):
     g = oracle.Graph(1, [0], [-1], [np.inf], [0.0], [0.0], [1.0], [1.0], [0.0])
-    r = oracle.em_step_injected(g, 0, 1.0, 1.0, 8, 50.0, [], [])
+    r = oracle.em_step_injected(g, 0, 1.0, 1.0, 8, [50.0], [])
     assert r["edge"] == 0 and r["x"] == 51.0
 
 
@@ -137,7 +137,7 @@ def test_exhaustive_one_step_enumeration(oracle):
                     # independently: first slot with u < T
                     ref = next(s for s in range(off[v], off[v + 1]) if u < int(T[s]))
                     assert exp_slot == ref
-                    r = oracle.em_step_injected(g, e, x0, 1e-4, 1, Wn, [u], [0.0])
+                    r = oracle.em_step_injected(g, e, x0, 1e-4, 1, [Wn], [u])
                     assert r["edge"] == se[ref]
                     assert r["x"] == (0.0 if send[ref] == 0 else L[se[ref]])
                     assert r["truncations"] == 1
@@ -148,16 +148,16 @@ def _trajectory_with_injection(oracle, g, edge, x, seed, steps, dt, M, flip_edge
     """Step one particle with the Philox draws passed in through the
     injection hook; on ``flip_edge`` the normal of an interior sub-step is
     negated (the flipped frame)."""
-    hits, fh, fl = 0, 0, 0
+    nd, hits, fh, fl = 0, 0, 0, 0
     out = []
     for t in range(steps):
-        Wn = oracle.main_normal(seed, 0, 0, t)
+        zs = [oracle.normal(seed, 0, 0, nd + i) for i in range(M + 1)]
         if flip_edge is not None and edge == flip_edge and 0.0 < x < length:
-            Wn = -Wn
-        draws = [oracle.split_draw(seed, 0, 0, hits + j) for j in range(M)]
-        r = oracle.em_step_injected(g, edge, x, dt, M, Wn, [d[0] for d in draws],
-                                    [d[1] for d in draws], hits, fh, fl)
-        edge, x, hits, fh, fl = r["edge"], r["x"], r["hits"], r["first_hits"], r["flags"]
+            zs[0] = -zs[0]
+        us = [oracle.split_draw(seed, 0, 0, hits + j) for j in range(M)]
+        r = oracle.em_step_injected(g, edge, x, dt, M, zs, us, nd, hits, fh, fl)
+        edge, x, nd, hits = r["edge"], r["x"], r["n_draw"], r["hits"]
+        fh, fl = r["first_hits"], r["flags"]
         out.append((edge, x))
     return out
 
@@ -192,12 +192,12 @@ def test_orientation_flip_mirrors_trajectories(oracle):
     assert matched >= 38
 
 
-def _run(oracle, d, n, steps, dt, M, seed=1, t0=0, pid=None, init=None):
+def _run(oracle, d, n, steps, dt, M, seed=1, pid=None, init=None):
     g = oracle.Graph.from_desc(d)
     e, x = init if init is not None else W.uniform_on_edges(d, n, 5)
     st = oracle.State(e, x, pid)
     cnt = oracle.Counters(g)
-    oracle.simulate(g, st, cnt, seed=seed, instance=0, t0=t0, dt=dt, steps=steps, M=M)
+    oracle.simulate(g, st, cnt, seed=seed, instance=0, dt=dt, steps=steps, M=M)
     return g, st, cnt
 
 
@@ -227,13 +227,13 @@ def test_chunking_and_sharding_bit_exact(oracle):
     b = oracle.State(*init)
     cb = oracle.Counters(g2)
     for c in range(4):
-        oracle.simulate(g2, b, cb, seed=1, instance=0, t0=30 * c, dt=3e-3, steps=30, M=5)
+        oracle.simulate(g2, b, cb, seed=1, instance=0, dt=3e-3, steps=30, M=5)
     # 2 shards by particle id
     s1 = oracle.State(init[0][:200], init[1][:200], np.arange(200))
     s2 = oracle.State(init[0][200:], init[1][200:], np.arange(200, n))
     cs = oracle.Counters(g2)
-    oracle.simulate(g2, s1, cs, seed=1, instance=0, t0=0, dt=3e-3, steps=120, M=5)
-    oracle.simulate(g2, s2, cs, seed=1, instance=0, t0=0, dt=3e-3, steps=120, M=5)
+    oracle.simulate(g2, s1, cs, seed=1, instance=0, dt=3e-3, steps=120, M=5)
+    oracle.simulate(g2, s2, cs, seed=1, instance=0, dt=3e-3, steps=120, M=5)
     for other, co in [(b, cb)]:
         assert np.array_equal(a.edge, other.edge) and np.array_equal(a.x, other.x)
         assert np.array_equal(a.hits, other.hits) and np.array_equal(ca.exits, co.exits)
