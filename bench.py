@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default="mixed")
+    ap.add_argument("--split-batch", type=int, default=0)
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--em-steps", type=int, default=EM_STEPS)
     ap.add_argument("--no-e2e", action="store_true")
@@ -68,7 +69,8 @@ def config(args, world):
             "potentials, sigma=sqrt(2), equal b, reflecting leaves",
             "n_particles_per_gpu": args.n, "global_particles": args.n * world,
             "dt": DT, "em_steps_per_step": args.em_steps, "M": M, "hist_bins_per_edge": BINS,
-            "precision": "fp32-mixed" if args.precision == "fp32" else "fp64",
+            "precision": {"mixed": "fp32 with fp64 hitting fraction and time left",
+                          "fp32": "fp32", "fp64": "fp64"}[args.precision],
             "parallelism": f"particle shards x{world}", "l2": "state 20 B/particle > L2"}
 
 
@@ -223,10 +225,12 @@ def run_ours(args):
     from paper_2512_02175_gb300 import binding as B
     B.load()
     B.use_torch_allocator()
-    prec = B.MG_FP32_MIXED if args.precision == "fp32" else B.MG_FP64
+    prec = {"mixed": B.MG_FP32_MIXED, "fp32": B.MG_FP32, "fp64": B.MG_FP64}[args.precision]
     stream = torch.cuda.Stream()
     g = B.Graph(desc)
     p = B.Particles(g, e0, x0, pid_base=rank * n, seed=SEED, precision=prec, stream=stream)
+    if args.split_batch:
+        p.set_tuning(split_batch=args.split_batch)
     hist = torch.zeros(g.n_edges * BINS, dtype=torch.int32, device="cuda")
 
     def step():
@@ -315,7 +319,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk,
             "launch_ms": launch_ms,

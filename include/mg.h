@@ -49,10 +49,11 @@ typedef enum {
 } mg_status;
 
 typedef enum {
-  MG_FP64 = 0,      /* every step in binary64 */
-  MG_FP32_MIXED = 1 /* positions, increments and normals in binary32; the
-                       hitting fraction and remaining time of a split in
-                       binary64; counts in integers */
+  MG_FP64 = 0,       /* every step in binary64 */
+  MG_FP32_MIXED = 1, /* positions, increments and normals in binary32; the
+                        hitting fraction alpha and the time left of a split
+                        in binary64; counts in integers */
+  MG_FP32 = 2        /* everything in binary32; counts in integers */
 } mg_precision;
 
 typedef enum { MG_VERTEX_STANDARD = 0, MG_VERTEX_ABSORBING = 1 } mg_vertex_kind;
@@ -60,6 +61,8 @@ typedef enum { MG_VERTEX_STANDARD = 0, MG_VERTEX_ABSORBING = 1 } mg_vertex_kind;
 /* Device-error bits reported with MG_ERR_DEVICE_FAULT. */
 #define MG_DEVERR_BAD_EDGE 1u  /* a particle's edge index out of range */
 #define MG_DEVERR_NAN 2u       /* a position became NaN or left [0, l_e] */
+#define MG_DEVERR_STREAM 4u    /* a particle used up its 2^32 - 16 normals */
+#define MG_DEVERR_STUCK 8u     /* the kernel's loop guard fired (a library bug) */
 
 /* Description of a metric graph (Definition 1; drift and diffusion of the
  * edge generator, Eq. (generator_edge); jump weights of the standard
@@ -128,17 +131,23 @@ mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge, uint8
 /* Creates a set of n particles on g (1 <= n <= 2^31 - 1).  edge0[n], x0[n]:
  * starting edges and positions, host arrays, or device arrays when
  * inputs_on_device != 0; 0 <= x0 <= l_e (x0 = 0 or l_e starts the particle at
- * that vertex).  Particle i has the global id pid_base + i (must not wrap
- * 2^32): its random numbers are Philox-4x32-10 (Salmon et al., SC'11) blocks
- * under the key (seed mod 2^32, seed >> 32) with counters
- *   (t >> 2, pid, 0, instance_id) for the normal of step t (lane t & 3) and
- *   (j, pid, 1, instance_id)      for the draws of its j-th vertex hit,
+ * that vertex).  Particle i has the global id pid = pid_base + i (must not
+ * wrap 2^32).  Its random numbers are Philox-4x32-10 (Salmon et al., SC'11)
+ * blocks under the key (seed mod 2^32, seed >> 32):
+ *   the n-th normal (one per Euler-Maruyama sub-step -- the first of a step
+ *   and each one after a split, in order) is Box-Muller of block
+ *   (n >> 2, pid, 0, instance_id): lanes n & 3 = 0..3 take r cos and r sin of
+ *   words (w0, w1), then of (w2, w3), with u = (2w + 1) 2^-33 (binary64) or
+ *   (2 (w >> 9) + 1) 2^-24 (binary32 modes);
+ *   the j-th vertex hit draws its next edge with word w0 of block
+ *   (j, pid, 1, instance_id),
  * so results do not depend on how particles are sharded or batched.  The
- * state holds, per particle: edge (-1 once absorbed), position x, hits,
- * first_hits (hits that started inside the edge), flags (bit 0: the FP64
- * trajectory passed within 1e-9 max(1, l_e) of a branch).  Step counter and
- * all counters start at 0.  Host inputs are validated
- * (MG_ERR_INVALID_ARG); device inputs are validated by the kernel. */
+ * state holds, per particle: edge (-1 once absorbed), position x, n_draw
+ * (normals used), hits, first_hits (hits that started inside the edge), flags
+ * (bit 0: the binary64 trajectory passed within 1e-9 max(1, l_e) of a
+ * branch).  Step counter and all counters start at 0.  Host inputs are
+ * validated (MG_ERR_INVALID_ARG); device inputs are validated by the kernel
+ * (reported by mg_synchronize). */
 mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edge0, const double* x0,
                             int inputs_on_device, uint32_t pid_base, uint64_t seed,
                             uint32_t instance_id, mg_precision precision, void* stream,
@@ -151,6 +160,12 @@ mg_status mg_particles_reset(mg_particles p, const int32_t* edge0, const double*
                              int inputs_on_device, void* stream);
 
 mg_status mg_particles_destroy(mg_particles p);
+
+/* Launch tuning of a set (the results do not depend on it): split_batch =
+ * pending vertex hits in a warp that trigger a batched split pass (1..32; 0:
+ * the library's default for the precision), steps_per_launch = largest number
+ * of EM-Steps per kernel launch (0: no limit beyond the library's own). */
+mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t steps_per_launch);
 
 /* Advances every particle by `steps` EM-Steps of length dt (Algorithm 2 of
  * the paper, with sub-steps from a vertex taken into the edge with |W| as in
@@ -196,15 +211,15 @@ mg_status mg_counters_reset(mg_particles p, void* stream);
 /* Checkpoint: copies the full particle state to host arrays (synchronises);
  * positions are returned in binary64.  step: EM-Steps taken so far.  Any
  * pointer may be NULL. */
-mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* hits,
+mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* n_draw, uint32_t* hits,
                        uint32_t* first_hits, uint32_t* flags, uint64_t* step, void* stream);
 
 /* Resume: overwrites the particle state from host arrays (all required) and
  * the step counter; with the counter-based random numbers the continuation is
  * bit-identical to an uninterrupted run. */
-mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x, const uint32_t* hits,
-                       const uint32_t* first_hits, const uint32_t* flags, uint64_t step,
-                       void* stream);
+mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x,
+                       const uint32_t* n_draw, const uint32_t* hits, const uint32_t* first_hits,
+                       const uint32_t* flags, uint64_t step, void* stream);
 
 /* n, precision and step counter of a set; any pointer may be NULL. */
 mg_status mg_particles_info(mg_particles p, int64_t* n, int32_t* precision, uint64_t* step);

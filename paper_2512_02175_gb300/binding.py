@@ -24,7 +24,7 @@ from . import _build
 
 MG_OK, MG_ERR_INVALID_ARG, MG_ERR_OUT_OF_MEMORY, MG_ERR_CUDA = 0, 1, 2, 3
 MG_ERR_TIMEOUT, MG_ERR_CANCELLED, MG_ERR_BUSY, MG_ERR_DEVICE_FAULT = 4, 5, 6, 7
-MG_FP64, MG_FP32_MIXED = 0, 1
+MG_FP64, MG_FP32_MIXED, MG_FP32 = 0, 1, 2
 MG_VERTEX_STANDARD, MG_VERTEX_ABSORBING = 0, 1
 _NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OUT_OF_MEMORY", 3: "MG_ERR_CUDA",
           4: "MG_ERR_TIMEOUT", 5: "MG_ERR_CANCELLED", 6: "MG_ERR_BUSY",
@@ -54,7 +54,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 # every symbol the C ABI declares (checked against include/mg.h by the tests)
 SYMBOLS = [
     "mg_set_allocator", "mg_graph_create", "mg_graph_destroy", "mg_graph_info", "mg_graph_slots",
-    "mg_particles_init", "mg_particles_reset", "mg_particles_destroy", "mg_simulate",
+    "mg_particles_init", "mg_particles_reset", "mg_particles_destroy", "mg_particles_set_tuning",
+    "mg_simulate",
     "mg_synchronize", "mg_histogram", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
     "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
 ]
@@ -96,13 +97,14 @@ def _declare(L):
         "mg_particles_init": ([vp, i64, vp, vp, C.c_int, u32, u64, u32, C.c_int, vp, C.POINTER(vp)], st),
         "mg_particles_reset": ([vp, vp, vp, C.c_int, vp], st),
         "mg_particles_destroy": ([vp], st),
+        "mg_particles_set_tuning": ([vp, i32, i64], st),
         "mg_simulate": ([vp, dbl, i64, i32, i32, vp, vp], st),
         "mg_synchronize": ([vp], st),
         "mg_histogram": ([vp, i32, vp, C.c_int, vp], st),
         "mg_exit_counts": ([vp, vp, vp, vp, vp, vp], st),
         "mg_counters_reset": ([vp, vp], st),
-        "mg_state_get": ([vp, vp, vp, vp, vp, vp, vp, vp], st),
-        "mg_state_set": ([vp, vp, vp, vp, vp, vp, u64, vp], st),
+        "mg_state_get": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
+        "mg_state_set": ([vp, vp, vp, vp, vp, vp, vp, u64, vp], st),
         "mg_particles_info": ([vp, vp, vp, vp], st),
         "mg_last_error": ([], C.c_char_p),
         "mg_version": ([], C.c_char_p),
@@ -258,6 +260,10 @@ def mg_particles_destroy(p):
     _check(load().mg_particles_destroy(p))
 
 
+def mg_particles_set_tuning(p, split_batch=0, steps_per_launch=0):
+    _check(load().mg_particles_set_tuning(p, int(split_batch), int(steps_per_launch)))
+
+
 def mg_particles_info(p):
     n, prec, step = C.c_int64(), C.c_int32(), C.c_uint64()
     _check(load().mg_particles_info(p, C.byref(n), C.byref(prec), C.byref(step)))
@@ -304,20 +310,21 @@ def mg_state_get(p, stream=None):
     n, _, _ = mg_particles_info(p)
     edge = np.zeros(n, np.int32)
     x = np.zeros(n, np.float64)
+    nd = np.zeros(n, np.uint32)
     hits = np.zeros(n, np.uint32)
     fh = np.zeros(n, np.uint32)
     fl = np.zeros(n, np.uint32)
     step = C.c_uint64()
-    _check(load().mg_state_get(p, _ptr(edge), _ptr(x), _ptr(hits), _ptr(fh), _ptr(fl),
+    _check(load().mg_state_get(p, _ptr(edge), _ptr(x), _ptr(nd), _ptr(hits), _ptr(fh), _ptr(fl),
                                C.byref(step), _stream_ptr(stream)))
-    return dict(edge=edge, x=x, hits=hits, first_hits=fh, flags=fl, step=step.value)
+    return dict(edge=edge, x=x, n_draw=nd, hits=hits, first_hits=fh, flags=fl, step=step.value)
 
 
 def mg_state_set(p, state, stream=None):
     a = {k: np.ascontiguousarray(state[k], dtype=dt) for k, dt in
-         [("edge", np.int32), ("x", np.float64), ("hits", np.uint32), ("first_hits", np.uint32),
-          ("flags", np.uint32)]}
-    _check(load().mg_state_set(p, _ptr(a["edge"]), _ptr(a["x"]), _ptr(a["hits"]),
+         [("edge", np.int32), ("x", np.float64), ("n_draw", np.uint32), ("hits", np.uint32),
+          ("first_hits", np.uint32), ("flags", np.uint32)]}
+    _check(load().mg_state_set(p, _ptr(a["edge"]), _ptr(a["x"]), _ptr(a["n_draw"]), _ptr(a["hits"]),
                                _ptr(a["first_hits"]), _ptr(a["flags"]), int(state["step"]),
                                _stream_ptr(stream)))
 
@@ -365,6 +372,9 @@ class Particles:
         self.precision = precision
         self.h = mg_particles_init(graph.h, edge0, x0, pid_base=pid_base, seed=seed,
                                    instance=instance, precision=precision, stream=stream)
+
+    def set_tuning(self, split_batch=0, steps_per_launch=0):
+        mg_particles_set_tuning(self.h, split_batch, steps_per_launch)
 
     def simulate(self, dt, steps, M, hist_bins=0, hist_out=None, stream=None):
         mg_simulate(self.h, dt, steps, M, hist_bins, hist_out, stream)

@@ -1,20 +1,29 @@
-// em_step_f32.cu -- binary32-mixed instantiation of the fused EM-Step kernel,
-// the histogram kernel and the state initialisation kernel.
+// em_step_f32.cu -- binary32-mixed and binary32 instantiations of the fused
+// EM-Step kernel, the binary32 histogram kernel and the state initialisation
+// kernels.
 #include "mg_em_step.cuh"
 #include "mg_launch.h"
 
 namespace mg {
 
-cudaError_t launch_em_step_f32(const SimArgs& a, size_t smem, cudaStream_t st) {
+template <int kMode>
+static cudaError_t launch_em(const SimArgs& a, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(em_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(em_step_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr = true;
   }
   const int64_t grid = (a.n + kBlock - 1) / kBlock;
-  em_step_kernel<false><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  em_step_kernel<kMode><<<(unsigned)grid, kBlock, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_em_step_mixed(const SimArgs& a, size_t smem, cudaStream_t st) {
+  return launch_em<kModeMixed>(a, smem, st);
+}
+cudaError_t launch_em_step_f32(const SimArgs& a, size_t smem, cudaStream_t st) {
+  return launch_em<kModeF32>(a, smem, st);
 }
 
 cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const void* x, int64_t n,
@@ -27,9 +36,9 @@ cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const 
   if (grid < 1) grid = 1;
   const size_t sh = smem ? align16((size_t)g.E * bins * 4) : 0;
   if (sh > 48 * 1024)
-    cudaFuncSetAttribute(histogram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(histogram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sh);
-  histogram_kernel<false><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
+  histogram_kernel<float><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -39,20 +48,21 @@ __global__ void init_state_kernel(GraphView g, const int32_t* __restrict__ edge0
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = edge0[i];
-    const double x = x0[i];  // may alias hits/first_hits: read before writing them
+    const double x = x0[i];
     uint32_t bad = 0;
     if (e < kDead || e >= g.E) bad |= kErrBadEdge;
     else if (e >= 0 && !(x >= 0.0 && x <= g.e64[e].L)) bad |= kErrNan;
     if (bad) atomicOr(err, bad);
     s.edge[i] = e;
     if (f64) reinterpret_cast<double*>(s.x)[i] = x;
-    else reinterpret_cast<float*>(s.x)[i] = (e >= 0 && x == g.e64[e].L) ? g.e32[e].L : (float)x;
+    else reinterpret_cast<float*>(s.x)[i] = (float)x;  // x <= l_e rounds to <= (float)l_e
   }
 }
 
 __global__ void zero_counters_kernel(StateView s, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    s.n_draw[i] = 0u;
     s.hits[i] = 0u;
     s.first_hits[i] = 0u;
     s.flags[i] = 0u;
@@ -61,8 +71,11 @@ __global__ void zero_counters_kernel(StateView s, int64_t n) {
 
 cudaError_t launch_init_state(const GraphView& g, const int32_t* edge0, const double* x0, int64_t n,
                               bool f64, StateView s, uint32_t* err, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = (n + kBlock - 1) / kBlock;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
   if (grid < 1) grid = 1;
   // x0 may live in the hits/first_hits storage: convert everything first,
   // then zero the counters in a second, stream-ordered kernel.

@@ -10,12 +10,12 @@ namespace mg {
 cudaError_t launch_em_step_f64(const SimArgs& a, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(em_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(em_step_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr = true;
   }
   const int64_t grid = (a.n + kBlock - 1) / kBlock;
-  em_step_kernel<true><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -29,9 +29,9 @@ cudaError_t launch_histogram_f64(const GraphView& g, const int32_t* edge, const 
   if (grid < 1) grid = 1;
   const size_t sh = smem ? align16((size_t)g.E * bins * 4) : 0;
   if (sh > 48 * 1024)
-    cudaFuncSetAttribute(histogram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(histogram_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sh);
-  histogram_kernel<true><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
+  histogram_kernel<double><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
   return cudaGetLastError();
 }
 

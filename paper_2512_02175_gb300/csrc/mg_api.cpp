@@ -17,6 +17,11 @@
 
 static_assert(MG_DEVERR_BAD_EDGE == mg::kErrBadEdge, "device error bits");
 static_assert(MG_DEVERR_NAN == mg::kErrNan, "device error bits");
+static_assert(MG_DEVERR_STREAM == mg::kErrStream, "device error bits");
+static_assert(MG_DEVERR_STUCK == mg::kErrStuck, "device error bits");
+static_assert((int)MG_FP64 == (int)mg::kModeF64 && (int)MG_FP32_MIXED == (int)mg::kModeMixed &&
+                  (int)MG_FP32 == (int)mg::kModeF32,
+              "precision modes");
 
 namespace {
 
@@ -308,7 +313,9 @@ struct mg_particles_s {
   uint32_t instance = 0;
   mg_precision prec = MG_FP64;
   uint64_t step = 0;
-  DevBuf state;      // edge | x | hits | first_hits | flags
+  int32_t split_batch = 0;       // 0: the library's default for the mode
+  int64_t steps_per_launch = 0;  // 0: as many as fit one launch
+  DevBuf state;      // edge | x | n_draw | hits | first_hits | flags
   DevBuf counters;   // exits[S] | absorbed[V] | trunc | psteps | err
   DevBuf hist_tmp;   // histogram staging for host output
   mg::StateView sv{};
@@ -328,6 +335,8 @@ void state_layout(mg_particles_s* p) {
   o = a256(o + 4 * (size_t)n);
   p->sv.x = b + o;
   o = a256(o + xbytes(p) * (size_t)n);
+  p->sv.n_draw = reinterpret_cast<uint32_t*>(b + o);
+  o = a256(o + 4 * (size_t)n);
   // hits and first_hits are adjacent: 8n contiguous bytes, 8-byte aligned,
   // reused as the binary64 staging area of host positions at initialisation
   p->sv.hits = reinterpret_cast<uint32_t*>(b + o);
@@ -337,7 +346,8 @@ void state_layout(mg_particles_s* p) {
 }
 
 size_t state_bytes(int64_t n, size_t xb) {
-  return a256(4 * (size_t)n) + a256(xb * (size_t)n) + a256(8 * (size_t)n) + a256(4 * (size_t)n);
+  return a256(4 * (size_t)n) + a256(xb * (size_t)n) + a256(4 * (size_t)n) + a256(8 * (size_t)n) +
+         a256(4 * (size_t)n);
 }
 
 void counter_layout(mg_particles_s* p) {
@@ -394,7 +404,7 @@ extern "C" mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edg
   if (n < 1 || n > 2147483647LL) return fail(MG_ERR_INVALID_ARG, "need 1 <= n <= 2^31 - 1");
   if ((uint64_t)pid_base + (uint64_t)n > 4294967296ull)
     return fail(MG_ERR_INVALID_ARG, "pid_base + n exceeds 2^32");
-  if (precision != MG_FP64 && precision != MG_FP32_MIXED)
+  if (precision != MG_FP64 && precision != MG_FP32_MIXED && precision != MG_FP32)
     return fail(MG_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mg_particles p = new mg_particles_s();
@@ -468,17 +478,40 @@ constexpr size_t kSmemBudget = 24 * 1024;
 
 }  // namespace
 
+extern "C" mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch,
+                                             int64_t steps_per_launch) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_particles_set_tuning: NULL particles");
+  if (split_batch < 0 || split_batch > 32)
+    return fail(MG_ERR_INVALID_ARG, "split_batch must be in [0, 32]");
+  if (steps_per_launch < 0) return fail(MG_ERR_INVALID_ARG, "steps_per_launch must be >= 0");
+  p->split_batch = split_batch;
+  p->steps_per_launch = steps_per_launch;
+  return MG_OK;
+}
+
+namespace {
+
+// Default number of pending lanes that triggers a batched split pass: larger
+// where the split path carries binary64 work, which costs the same per warp
+// instruction however many lanes are active.
+int32_t default_split_batch(mg_precision prec) {
+  switch (prec) {
+    case MG_FP32: return 8;
+    case MG_FP32_MIXED: return 12;
+    default: return 8;
+  }
+}
+
+}  // namespace
+
 extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t M,
                                  int32_t hist_bins, uint32_t* hist_out, void* stream) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_simulate: NULL particles");
   if (!(std::isfinite(dt) && dt > 0.0)) return fail(MG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (steps < 0) return fail(MG_ERR_INVALID_ARG, "steps must be >= 0");
-  if (M < 1) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be >= 1");
+  if (M < 1 || M > 1024) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be in [1, 1024]");
   if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");
   if (hist_bins > 0 && !hist_out) return fail(MG_ERR_INVALID_ARG, "hist_bins > 0 needs hist_out");
-  // the step index t enters the Philox counter as t >> 2 in 32 bits
-  if (p->step + (uint64_t)steps > (1ull << 34))
-    return fail(MG_ERR_INVALID_ARG, "step counter would exceed 2^34");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mg_graph g = p->g;
   const bool f64 = p->prec == MG_FP64;
@@ -498,42 +531,46 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   a.dt = dt;
   a.sqrt_dt = std::sqrt(dt);
   a.M = M;
-  // shared-memory plan: stage the tables, then the counters, then the
-  // histogram, as long as the total stays within the budget
+  a.split_batch = p->split_batch > 0 ? p->split_batch : default_split_batch(p->prec);
+  // shared-memory plan: the normal ring always; then the tables, the
+  // counters and the histogram, as long as the total stays in the budget
   const bool want_hist = hist_bins > 0;
   const int32_t hist_len = want_hist ? g->E * hist_bins : 0;
   bool stage = true, counters = true, shist = want_hist;
-  auto lay = [&]() {
-    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters, shist ? hist_len : 0).total;
+  auto lay = [&](bool with_hist) {
+    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
+                           (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
   };
-  if (lay() > kSmemBudget) shist = false;
-  if (lay() > kSmemBudget) counters = false;
-  if (lay() > kSmemBudget) stage = false;
-  if (lay() > kSmemBudget) counters = false;
+  const size_t budget = kSmemBudget + (f64 ? 8u : 4u) * 8u * mg::kBlock;
+  if (lay(true) > budget) shist = false;
+  if (lay(true) > budget) counters = false;
+  if (lay(true) > budget) stage = false;
   a.stage_smem = stage;
   a.smem_counters = counters;
-  a.smem_hist = shist;
-  const size_t smem = lay();
-  // 32-bit shared counters: a block of 256 particles adds at most 256 M per
-  // step to one counter; split the launch so that cannot wrap
-  int64_t chunk = steps;
+  // launches: at most 2^31 - 1 steps (the per-lane step counter), and with
+  // 32-bit shared counters at most 2^32 / (256 (2M + 1)) so they cannot wrap
+  int64_t chunk = 2147483647LL;
   if (counters) {
-    const int64_t cap = (int64_t)(4294967295ull / (256ull * (uint64_t)M));
+    const int64_t cap = (int64_t)(4294967295ull / (256ull * (2ull * (uint64_t)M + 1ull)));
     if (chunk > cap) chunk = cap;
   }
+  if (p->steps_per_launch > 0 && p->steps_per_launch < chunk) chunk = p->steps_per_launch;
   if (chunk < 1) chunk = 1;
   int64_t done = 0;
   do {
     const int64_t now = (steps - done < chunk) ? steps - done : chunk;
-    a.t_begin = p->step + (uint64_t)done;
     a.steps = now;
     const bool last = done + now >= steps;
     a.hist_bins = (last && want_hist) ? hist_bins : 0;
     a.hist = hist_out;
     a.smem_hist = (last && shist) ? 1 : 0;
-    const size_t sm = (last && shist) ? smem
-                      : mg::smem_layout(g->V, g->E, g->S, f64, stage, counters, 0).total;
-    cudaError_t ce = f64 ? mg::launch_em_step_f64(a, sm, st) : mg::launch_em_step_f32(a, sm, st);
+    const size_t sm = lay(last);
+    cudaError_t ce;
+    switch (p->prec) {
+      case MG_FP64: ce = mg::launch_em_step_f64(a, sm, st); break;
+      case MG_FP32_MIXED: ce = mg::launch_em_step_mixed(a, sm, st); break;
+      default: ce = mg::launch_em_step_f32(a, sm, st); break;
+    }
     if (ce != cudaSuccess) return cuda_fail(ce, "mg_simulate: launch");
     done += now;
   } while (done < steps);
@@ -550,7 +587,7 @@ extern "C" mg_status mg_synchronize(mg_particles p) {
   if (err) {
     MG_CUDA(cudaMemset(p->cv.err, 0, 4));
     return fail(MG_ERR_DEVICE_FAULT, "device error bits 0x%x (1: edge out of range, 2: position "
-                "outside [0, l_e] or NaN)", err);
+                "outside [0, l_e] or NaN, 4: random stream exhausted, 8: loop guard)", err);
   }
   return MG_OK;
 }
@@ -609,9 +646,9 @@ extern "C" mg_status mg_counters_reset(mg_particles p, void* stream) {
   return MG_OK;
 }
 
-extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* hits,
-                                  uint32_t* first_hits, uint32_t* flags, uint64_t* step,
-                                  void* stream) {
+extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* n_draw,
+                                  uint32_t* hits, uint32_t* first_hits, uint32_t* flags,
+                                  uint64_t* step, void* stream) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_state_get: NULL particles");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)p->n;
@@ -625,6 +662,7 @@ extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint
       MG_CUDA(cudaMemcpyAsync(xf.data(), p->sv.x, 4 * n, cudaMemcpyDeviceToHost, st));
     }
   }
+  if (n_draw) MG_CUDA(cudaMemcpyAsync(n_draw, p->sv.n_draw, 4 * n, cudaMemcpyDeviceToHost, st));
   if (hits) MG_CUDA(cudaMemcpyAsync(hits, p->sv.hits, 4 * n, cudaMemcpyDeviceToHost, st));
   if (first_hits)
     MG_CUDA(cudaMemcpyAsync(first_hits, p->sv.first_hits, 4 * n, cudaMemcpyDeviceToHost, st));
@@ -637,9 +675,10 @@ extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint
 }
 
 extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x,
-                                  const uint32_t* hits, const uint32_t* first_hits,
-                                  const uint32_t* flags, uint64_t step, void* stream) {
-  if (!p || !edge || !x || !hits || !first_hits || !flags)
+                                  const uint32_t* n_draw, const uint32_t* hits,
+                                  const uint32_t* first_hits, const uint32_t* flags,
+                                  uint64_t step, void* stream) {
+  if (!p || !edge || !x || !n_draw || !hits || !first_hits || !flags)
     return fail(MG_ERR_INVALID_ARG, "mg_state_set: NULL argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)p->n;
@@ -659,6 +698,7 @@ extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const dou
     for (size_t i = 0; i < n; ++i) xf[i] = (float)x[i];
     MG_CUDA(cudaMemcpyAsync(p->sv.x, xf.data(), 4 * n, cudaMemcpyHostToDevice, st));
   }
+  MG_CUDA(cudaMemcpyAsync(p->sv.n_draw, n_draw, 4 * n, cudaMemcpyHostToDevice, st));
   MG_CUDA(cudaMemcpyAsync(p->sv.hits, hits, 4 * n, cudaMemcpyHostToDevice, st));
   MG_CUDA(cudaMemcpyAsync(p->sv.first_hits, first_hits, 4 * n, cudaMemcpyHostToDevice, st));
   MG_CUDA(cudaMemcpyAsync(p->sv.flags, flags, 4 * n, cudaMemcpyHostToDevice, st));

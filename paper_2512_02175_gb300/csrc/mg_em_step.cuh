@@ -4,24 +4,36 @@
 // EM-Steps of the timestep-splitting Euler-Maruyama scheme ("Sampling on
 // Metric Graphs", Algorithms 1 and 2), keeping the particle in registers for
 // the whole launch (Section 3.1: state in registers, global memory only for
-// the ensemble statistics).  Per step:
+// the ensemble statistics).
 //
-//   fast path  one Euler-Maruyama sub-step x + mu_e(x) dt + sigma_e sqrt(dt) W
-//              that stays inside (0, l_e): two FMAs and two compares, with W
-//              from a Philox-4x32-10 block shared by four consecutive steps.
-//   slow path  the sub-step leaves the edge (or starts at a vertex): solve for
-//              the hitting fraction alpha, keep (1 - alpha) h, draw the next
-//              edge from b_v with an integer threshold table, restart from the
-//              vertex with |W| into the new edge, repeat up to M times.
+// Every Euler-Maruyama sub-step -- the first of a step, and each one that
+// continues a step from a vertex after a split -- takes the next normal of
+// the particle's own counter-based stream (Philox-4x32-10 + Box-Muller, four
+// normals per block), buffered per thread in an 8-deep ring in shared memory.
+// The loop runs one sub-step per lane per iteration:
+//
+//   sub-step  x~ = x + mu_e(x) h + sigma_e sqrt(h) W: two FMAs with per-lane
+//             coefficients (h = dt, or the time left after a split; W = +-|z|
+//             when the sub-step starts at a vertex).  If x~ stays inside
+//             (0, l_e) the sub-step is done.
+//   split     otherwise the lane is marked pending and waits.  The warp
+//             resolves its pending lanes together -- once enough are waiting,
+//             or when no other lane can move -- so the long split path
+//             (hitting fraction, time left, jump draw, next edge) runs with
+//             many lanes active instead of one.  A particle's draws depend
+//             only on its own counters, so batching does not change results.
 //
 // Counters (exits per slot, absorptions, truncations) and the optional
 // snapshot histogram are privatised in shared memory when they fit and
 // flushed with one atomic per nonzero entry per block.
 //
-// Precision: kF64 = true computes everything in binary64 in the same order as
-// the plain CPU reference (the translation unit is built without FMA
-// contraction); kF64 = false keeps positions, increments and normals in
-// binary32 and only the hitting fraction and remaining time in binary64.
+// Precision modes (template kMode):
+//   kModeF64    everything in binary64, in the same operation order as the
+//               plain CPU reference (the translation unit is built without
+//               FMA contraction);
+//   kModeMixed  positions, increments and normals in binary32; the hitting
+//               fraction alpha = s^2 and the time left h in binary64;
+//   kModeF32    everything in binary32.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -76,9 +88,10 @@ __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double&
 }
 
 // binary32: u = (2 (w >> 9) + 1) 2^-24, formed exactly from the top 23 bits
-// (1 + m 2^-23 minus 1 - 2^-24), so the FP32 and FP64 modes see the same
-// words.  cos(2 pi u) = -cos(2 pi u - pi) keeps the hardware sine/cosine on
-// (-pi, pi).  lg2/sqrt/sin/cos are the approximate hardware instructions.
+// (1 + m 2^-23 minus 1 - 2^-24), so the binary32 and binary64 modes see the
+// same words.  cos(2 pi u) = -cos(2 pi u - pi) keeps the hardware
+// sine/cosine on (-pi, pi).  lg2/sqrt/sin/cos are the approximate hardware
+// instructions.
 __device__ __forceinline__ float u01_f32(uint32_t w) {
   return __uint_as_float((w >> 9) | 0x3f800000u) - 0.99999994f;
 }
@@ -94,83 +107,43 @@ __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& 
   zs = -r * s;
 }
 
-template <bool kF64>
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb,
-                                           std::conditional_t<kF64, double, float>& zc,
-                                           std::conditional_t<kF64, double, float>& zs) {
-  if constexpr (kF64) box_muller_f64(wa, wb, zc, zs);
-  else box_muller_f32(wa, wb, zc, zs);
-}
-
 // ---------------------------------------------------- hitting-fraction root
 
 // First root s in [0, 1] of A s^2 + B s + C = 0 with C >= 0 (s = sqrt(alpha)
 // of the partial step): A = 0 gives -C/B; otherwise (-B - d)/(2A) for B > 0
 // and the equal 2C/(-B + d) for B <= 0, each free of cancellation on its
 // side; d = sqrt(max(B^2 - 4AC, 0)); the result is clamped to [0, 1].
-__device__ __forceinline__ double hit_root(double A, double B, double C) {
-  double s;
-  if (A == 0.0) {
-    s = (B == 0.0) ? 0.0 : -C / B;
+template <typename T>
+__device__ __forceinline__ T hit_root(T A, T B, T C) {
+  T s;
+  if (A == T(0)) {
+    s = (B == T(0)) ? T(0) : -C / B;
   } else {
-    const double disc = B * B - 4.0 * A * C;
-    const double d = sqrt(disc > 0.0 ? disc : 0.0);
-    if (B > 0.0) {
-      s = (-B - d) / (2.0 * A);
+    const T disc = B * B - T(4) * A * C;
+    const T d = sqrt(disc > T(0) ? disc : T(0));
+    if (B > T(0)) {
+      s = (-B - d) / (T(2) * A);
     } else {
-      const double den = -B + d;
-      s = (den == 0.0) ? 0.0 : (2.0 * C) / den;
+      const T den = -B + d;
+      s = (den == T(0)) ? T(0) : (T(2) * C) / den;
     }
   }
-  if (!(s > 0.0)) s = 0.0;
-  if (s > 1.0) s = 1.0;
+  if (!(s > T(0))) s = T(0);
+  if (s > T(1)) s = T(1);
   return s;
 }
 
-// --------------------------------------------------------------- the edge
-
-template <bool kF64>
-struct EdgeRegs {
-  using R = std::conditional_t<kF64, double, float>;
-  R L, c0, c1, sigma;
-  int32_t src, dst, slot_init, slot_term;
-  // fast-path coefficients for a full step of length dt (FP32 mode):
-  // x + (c0 + c1 x) dt + sigma sqrt(dt) W = x Q + P + S W
-  float P, Q, S;
-};
-
-template <bool kF64>
-__device__ __forceinline__ void load_edge(const GraphView& g, int32_t e, double dt,
-                                          double sqrt_dt, EdgeRegs<kF64>& r) {
-  if constexpr (kF64) {
-    const EdgeRec64 q = g.e64[e];
-    r.L = q.L; r.c0 = q.c0; r.c1 = q.c1; r.sigma = q.sigma;
-    r.src = q.src; r.dst = q.dst; r.slot_init = q.slot_init; r.slot_term = q.slot_term;
-  } else {
-    const EdgeRec32 q = g.e32[e];
-    r.L = q.L; r.c0 = q.c0; r.c1 = q.c1; r.sigma = q.sigma;
-    r.src = q.src; r.dst = q.dst; r.slot_init = q.slot_init; r.slot_term = q.slot_term;
-    r.P = q.c0 * (float)dt;
-    r.Q = fmaf(q.c1, (float)dt, 1.0f);
-    r.S = q.sigma * (float)sqrt_dt;
-  }
-}
-
-// Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j.
+// Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j
+// (thresholds are non-decreasing and the last is 2^32 > u).
 __device__ __forceinline__ int32_t choose_slot(const GraphView& g, const VtxRec& vr, uint32_t u) {
-  int32_t lo = vr.begin, hi = vr.end - 1;  // the last threshold is 2^32 > u
-  while (lo < hi) {  // thresholds are non-decreasing: binary search
+  int32_t lo = vr.begin, hi = vr.end - 1;
+  while (lo < hi) {
     const int32_t mid = (lo + hi) >> 1;
     if ((uint64_t)u < g.slot[mid].T) hi = mid;
     else lo = mid + 1;
   }
   return lo;
 }
-
-// Per-thread accumulators that are reduced once per block.
-struct ThreadCounters {
-  uint32_t trunc;
-};
 
 struct BlockCounters {
   uint32_t* exits;     // shared [S] or nullptr (then global atomics)
@@ -188,138 +161,259 @@ __device__ __forceinline__ void count_absorbed(const CounterView& c, const Block
   else atomicAdd(&c.absorbed[v], 1ull);
 }
 
-// ------------------------------------------------------------ the EM-Step
+// ---------------------------------------------------------------- the lane
 
-template <bool kF64>
-struct Particle {
-  using R = std::conditional_t<kF64, double, float>;
-  int32_t e;
-  R x;
-  bool at_v;  // x is an endpoint of e: the particle sits at that vertex
-  uint32_t hits, first_hits, flags;
-  EdgeRegs<kF64> ed;
+template <int kMode>
+struct Types {
+  using R = std::conditional_t<kMode == kModeF64, double, float>;  // positions, normals
+  using H = std::conditional_t<kMode == kModeF32, float, double>;  // alpha, time left
 };
 
-// The whole EM-Step from its first sub-step on, once that sub-step is known
-// to leave the edge or to start at a vertex (Algorithm 2, with the |W| rule of
-// Algorithm 1 for sub-steps from a vertex).  W: the step's first normal.
-__device__ __forceinline__ float absr(float v) { return fabsf(v); }
-__device__ __forceinline__ double absr(double v) { return fabs(v); }
+// Sign handling of the normal of a sub-step: W = (z & wand) | wor on the sign
+// bit (z itself inside an edge, +|z| at an init end, -|z| at a term end).
+__device__ __forceinline__ float apply_sign(float z, uint32_t wand, uint32_t wor) {
+  return __uint_as_float((__float_as_uint(z) & wand) | wor);
+}
+__device__ __forceinline__ double apply_sign(double z, uint32_t wand, uint32_t wor) {
+  const int lo = __double2loint(z);
+  const int hi = (int)(((uint32_t)__double2hiint(z) & wand) | wor);
+  return __hiloint2double(hi, lo);
+}
 
-template <bool kF64>
-__device__ __forceinline__ void em_step_split(Particle<kF64>& p, std::conditional_t<kF64, double, float> W,
-                                           const SimArgs& a, const GraphView& g,
-                                           const BlockCounters& bc, ThreadCounters& tc,
-                                           uint32_t pid) {
-  using R = std::conditional_t<kF64, double, float>;
-  double h = a.dt;  // time left in this step (binary64 in both modes)
-  int32_t k = 0;    // splits taken in this step
-  for (;;) {
-    int32_t at_end = -1;
-    if (p.at_v) at_end = (p.x == (R)0) ? kEndInit : kEndTerm;
-    if (at_end == kEndInit) W = absr(W);
-    else if (at_end == kEndTerm) W = -absr(W);
+template <int kMode>
+struct Lane {
+  using R = typename Types<kMode>::R;
+  using H = typename Types<kMode>::H;
+  // particle
+  int32_t e;
+  R x;
+  uint32_t n_draw, n_gen, hits, first_hits, flags;
+  // current edge
+  R L;
+  R tol;  // binary64 mode: branch margin 1e-9 max(1, l_e)
+  // sub-step coefficients for the time h of the current sub-step:
+  //   binary32: x~ = x Q + P + S W, P = c0 h, Q = 1 + c1 h, S = sigma sqrt(h)
+  //   binary64: x~ = (x + (c0 + c1 x) h) + S W, S = sigma sqrt(h)
+  R P, Q, S;
+  R Pm, Qm, Sm;  // the same for a whole step (h = dt)
+  R c0, c1;      // binary64 mode
+  H h;           // time left in the current step
+  uint32_t wand, wor;
+  int32_t cur_slot;  // slot of the vertex end the particle sits at
+  int32_t k;         // splits in the current step
+  uint32_t left;     // steps left in this launch
+  bool at_v, in_cont, pending, active;
+  R Wp, xtp;  // normal and end point of the pending sub-step
+};
 
-    // Euler-Maruyama sub-step over the time left
-    const R xs = p.x;
-    R a_, b_, xt;
-    if constexpr (kF64) {
-      const double mu = p.ed.c0 + p.ed.c1 * xs;
-      a_ = mu * h;
-      b_ = p.ed.sigma * sqrt(h) * W;
-      xt = xs + a_ + b_;
-      const double L = p.ed.L;
-      const double tol = 1e-9 * ((isfinite(L) && L > 1.0) ? L : 1.0);
-      if (fabs(xt) < tol || (isfinite(L) && fabs(L - xt) < tol)) p.flags |= 1u;
-    } else {
-      const float hf = (float)h;
-      const float mu = fmaf(p.ed.c1, xs, p.ed.c0);
-      a_ = mu * hf;
-      b_ = p.ed.sigma * sqrtf(hf) * W;
-      xt = xs + a_ + b_;
-    }
-    if (xt > (R)0 && xt < p.ed.L) {  // stays inside the open edge
-      if (at_end >= 0) {
-        const int32_t slot = (at_end == kEndInit) ? p.ed.slot_init : p.ed.slot_term;
-        count_exit(a.c, bc, slot);
-      }
-      p.x = xt;
-      p.at_v = false;
-      return;
-    }
+template <int kMode>
+__device__ __forceinline__ void set_vertex_sign(Lane<kMode>& p, int32_t end) {
+  p.wand = 0x7fffffffu;
+  p.wor = (end == kEndInit) ? 0u : 0x80000000u;
+}
 
-    // vertex hit: partial step to the vertex (binary64)
-    const bool hit_init = !(xt > (R)0);
-    const int32_t v = hit_init ? p.ed.src : p.ed.dst;
-    const double A = hit_init ? (double)a_ : -(double)a_;
-    const double B = hit_init ? (double)b_ : -(double)b_;
-    const double C = hit_init ? (double)xs : (double)p.ed.L - (double)xs;
-    const double s = hit_root(A, B, C);
-    const double alpha = s * s;
-    h = (1.0 - alpha) * h;
-    if constexpr (kF64) {
-      if (h < 1e-9 * a.dt) p.flags |= 1u;
-    }
-    const uint32_t j = p.hits;
-    p.hits = j + 1u;
-    if (at_end < 0) p.first_hits++;
-    ++k;
-
-    const VtxRec vr = g.vtx[v];
-    if (vr.kind == kVertexAbsorbing) {
-      count_absorbed(a.c, bc, v);
-      p.e = kDead;
-      return;
-    }
-    // draws of the j-th hit: u = w0 picks the slot, (w2, w3) the next normal
-    const U4 w = philox4x32_10(j, pid, 1u, a.instance, a.rk);
-    const int32_t slot = choose_slot(g, vr, w.x);
-    const SlotRec sr = g.slot[slot];
-    p.e = sr.edge;
-    load_edge<kF64>(g, p.e, a.dt, a.sqrt_dt, p.ed);
-    p.x = (sr.end == kEndInit) ? (R)0 : p.ed.L;
-    p.at_v = true;
-    if (k == a.M) {  // split cap: stay at the vertex (Theorem 1)
-      tc.trunc++;
-      return;
-    }
-    if (h <= 0.0) return;
-    R zc, zs;
-    box_muller<kF64>(w.z, w.w, zc, zs);
-    W = zc;
+// Load edge e into the lane and set its whole-step coefficients (h = dt).
+template <int kMode>
+__device__ __forceinline__ void enter_edge(Lane<kMode>& p, const GraphView& g, int32_t e,
+                                           const SimArgs& a) {
+  p.e = e;
+  if constexpr (kMode == kModeF64) {
+    const EdgeRec64& q = g.e64[e];
+    p.L = q.L;
+    p.c0 = q.c0;
+    p.c1 = q.c1;
+    p.Sm = q.sigma * a.sqrt_dt;
+    p.tol = 1e-9 * ((isfinite(q.L) && q.L > 1.0) ? q.L : 1.0);
+  } else {
+    const EdgeRec32& q = g.e32[e];
+    p.L = q.L;
+    p.Pm = q.c0 * (float)a.dt;
+    p.Qm = fmaf(q.c1, (float)a.dt, 1.0f);
+    p.Sm = q.sigma * (float)a.sqrt_dt;
   }
 }
 
-// One EM-Step with its first normal W: the fast interior sub-step, else the
-// split path.  Returns false once the particle is absorbed.
-template <bool kF64>
-__device__ __forceinline__ bool em_step(Particle<kF64>& p, std::conditional_t<kF64, double, float> W,
-                                        const SimArgs& a, const GraphView& g,
-                                        const BlockCounters& bc, ThreadCounters& tc, uint32_t pid) {
-  using R = std::conditional_t<kF64, double, float>;
-  R xt;
-  if constexpr (kF64) {
-    const double mu = p.ed.c0 + p.ed.c1 * p.x;
-    const double a_ = mu * a.dt;
-    const double b_ = p.ed.sigma * a.sqrt_dt * W;
-    xt = p.x + a_ + b_;
-  } else {
-    xt = fmaf(p.ed.S, W, fmaf(p.x, p.ed.Q, p.ed.P));
+template <int kMode>
+__device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimArgs& a) {
+  p.h = (typename Types<kMode>::H)a.dt;
+  if constexpr (kMode != kModeF64) {
+    p.P = p.Pm;
+    p.Q = p.Qm;
   }
-  if (!p.at_v && xt > (R)0 && xt < p.ed.L) {
-    if constexpr (kF64) {
-      const double L = p.ed.L;
-      const double tol = 1e-9 * ((isfinite(L) && L > 1.0) ? L : 1.0);
-      if (fabs(xt) < tol || (isfinite(L) && fabs(L - xt) < tol)) p.flags |= 1u;
+  p.S = p.Sm;
+}
+
+// Coefficients of a sub-step over the time left h on the current edge.
+template <int kMode>
+__device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const GraphView& g) {
+  if constexpr (kMode == kModeF64) {
+    p.S = g.e64[p.e].sigma * sqrt(p.h);
+  } else {
+    const EdgeRec32& q = g.e32[p.e];
+    const float hf = (float)p.h;
+    p.P = q.c0 * hf;
+    p.Q = fmaf(q.c1, hf, 1.0f);
+    p.S = q.sigma * sqrtf(hf);
+  }
+}
+
+// Ring of buffered normals: normal n of the thread at ring[(n & 7) * bd + tid].
+// A stream never wraps: a lane that would pass 2^32 - 16 normals stops with
+// kErrStream.
+template <int kMode>
+__device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R* ring,
+                                       const SimArgs& a, uint32_t pid) {
+  using R = typename Types<kMode>::R;
+  if (p.n_gen >= 0xFFFFFFF0u) {
+    atomicOr(a.c.err, kErrStream);
+    p.active = false;
+    p.pending = false;
+    return;
+  }
+  const U4 w = philox4x32_10(p.n_gen >> 2, pid, 0u, a.instance, a.rk);
+  R z0, z1, z2, z3;
+  if constexpr (kMode == kModeF64) {
+    box_muller_f64(w.x, w.y, z0, z1);
+    box_muller_f64(w.z, w.w, z2, z3);
+  } else {
+    box_muller_f32(w.x, w.y, z0, z1);
+    box_muller_f32(w.z, w.w, z2, z3);
+  }
+  const uint32_t bd = blockDim.x, tid = threadIdx.x;
+  const uint32_t s0 = p.n_gen & 7u;  // 0 or 4
+  ring[(s0 + 0) * bd + tid] = z0;
+  ring[(s0 + 1) * bd + tid] = z1;
+  ring[(s0 + 2) * bd + tid] = z2;
+  ring[(s0 + 3) * bd + tid] = z3;
+  p.n_gen += 4;
+}
+
+// One Euler-Maruyama sub-step with the next normal.  Leaves the lane pending
+// when the sub-step ends outside (0, l_e).
+template <int kMode>
+__device__ __forceinline__ void sub_step(Lane<kMode>& p, const typename Types<kMode>::R* ring,
+                                         const SimArgs& a, const BlockCounters& bc) {
+  using R = typename Types<kMode>::R;
+  const R z = ring[(p.n_draw & 7u) * blockDim.x + threadIdx.x];
+  p.n_draw++;
+  const R W = apply_sign(z, p.wand, p.wor);
+  R xt;
+  if constexpr (kMode == kModeF64) {
+    const double mu = p.c0 + p.c1 * p.x;
+    const double a_ = mu * p.h;
+    const double b_ = p.S * W;
+    xt = p.x + a_ + b_;
+    if (fabs(xt) < p.tol || (isfinite(p.L) && fabs(p.L - xt) < p.tol)) p.flags |= 1u;
+  } else {
+    xt = fmaf(p.S, W, fmaf(p.x, p.Q, p.P));
+  }
+  if (xt > R(0) && xt < p.L) {
+    if (p.at_v | p.in_cont) {
+      if (p.at_v) count_exit(a.c, bc, p.cur_slot);  // left the vertex into the edge
+      if (p.in_cont) use_step_coefficients(p, a);   // the step is complete
+      p.at_v = false;
+      p.in_cont = false;
+      p.wand = 0xffffffffu;
+      p.wor = 0u;
     }
     p.x = xt;
-    return true;
+    p.k = 0;
+    if (--p.left == 0) p.active = false;
+  } else {
+    p.pending = true;
+    p.Wp = W;
+    p.xtp = xt;
   }
-  em_step_split<kF64>(p, W, a, g, bc, tc, pid);
-  return p.e >= 0;
 }
 
-// ---------------------------------------------------------- shared staging
+// Resolve the pending vertex hit: partial step to the vertex, time left,
+// jump draw, next edge, and the coefficients of the rest of the step.
+template <int kMode>
+__device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
+                                      const BlockCounters& bc, uint32_t pid, uint32_t& trunc) {
+  using R = typename Types<kMode>::R;
+  using H = typename Types<kMode>::H;
+  p.pending = false;
+  const R xs = p.x;
+  const bool hit_init = !(p.xtp > R(0));
+  int32_t v;
+  if constexpr (kMode == kModeF64) {
+    const double mu = p.c0 + p.c1 * xs;
+    const double a_ = mu * p.h;
+    const double b_ = p.S * p.Wp;
+    const double A = hit_init ? a_ : -a_;
+    const double B = hit_init ? b_ : -b_;
+    const double C = hit_init ? xs : p.L - xs;
+    const double s = hit_root<double>(A, B, C);
+    const double alpha = s * s;
+    p.h = (1.0 - alpha) * p.h;
+    if (p.h < 1e-9 * a.dt) p.flags |= 1u;
+    v = hit_init ? g.e64[p.e].src : g.e64[p.e].dst;
+  } else {
+    // increments of the pending sub-step in binary32: a = mu(x) h, b = S W
+    const EdgeRec32& q = g.e32[p.e];
+    const float hf = (float)p.h;
+    const float a_ = fmaf(q.c1, xs, q.c0) * hf;
+    const float b_ = p.S * p.Wp;
+    const float A = hit_init ? a_ : -a_;
+    const float B = hit_init ? b_ : -b_;
+    const float C = hit_init ? xs : p.L - xs;
+    const float s = hit_root<float>(A, B, C);
+    if constexpr (kMode == kModeMixed) {
+      const double sd = (double)s;
+      const double alpha = sd * sd;   // binary64 hitting fraction
+      p.h = fma(-alpha, p.h, p.h);    // binary64 time left
+    } else {
+      p.h = fmaf(-s * s, p.h, p.h);
+    }
+    v = hit_init ? q.src : q.dst;
+  }
+  const uint32_t j = p.hits;
+  p.hits = j + 1u;
+  if (!p.at_v) p.first_hits++;
+  p.k++;
+  const VtxRec vr = g.vtx[v];
+  if (vr.kind == kVertexAbsorbing) {
+    count_absorbed(a.c, bc, v);
+    p.e = kDead;
+    p.active = false;
+    return;
+  }
+  const U4 w = philox4x32_10(j, pid, 1u, a.instance, a.rk);
+  const int32_t slot = choose_slot(g, vr, w.x);
+  const SlotRec sr = g.slot[slot];
+  enter_edge<kMode>(p, g, sr.edge, a);
+  p.x = (sr.end == kEndInit) ? R(0) : p.L;
+  p.at_v = true;
+  p.cur_slot = slot;
+  set_vertex_sign(p, sr.end);
+  if (p.k == a.M || !(p.h > (H)0)) {  // the step ends at the vertex
+    if (p.k == a.M) trunc++;
+    p.k = 0;
+    p.in_cont = false;
+    use_step_coefficients(p, a);
+    if (--p.left == 0) p.active = false;
+    return;
+  }
+  p.in_cont = true;
+  use_rest_coefficients(p, g);
+}
+
+// Histogram bin of position x on edge e (the set's precision):
+// min(floor(x * (bins / range_e)), bins - 1), floored at 0.
+template <typename R>
+__device__ __forceinline__ int32_t hist_bin(R x, double range, int32_t bins) {
+  const double scale = (double)bins / range;
+  int32_t b;
+  if constexpr (std::is_same<R, double>::value) {
+    const double f = floor(x * scale);
+    b = (f < 0.0) ? 0 : (f > (double)(bins - 1)) ? bins - 1 : (int32_t)f;
+  } else {
+    const float f = floorf(x * (float)scale);
+    b = (f < 0.0f) ? 0 : (f > (float)(bins - 1)) ? bins - 1 : (int32_t)f;
+  }
+  return b;
+}
 
 template <typename T>
 __device__ __forceinline__ void block_copy(T* dst, const T* src, int32_t n) {
@@ -334,32 +428,17 @@ __device__ __forceinline__ void block_zero(T* dst, int32_t n) {
   for (int32_t k = threadIdx.x; k < n; k += blockDim.x) dst[k] = 0;
 }
 
-// Histogram bin of position x on edge e (the set's precision):
-// min(floor(x * (bins / range_e)), bins - 1), floored at 0.
-template <bool kF64>
-__device__ __forceinline__ int32_t hist_bin(std::conditional_t<kF64, double, float> x, double range,
-                                            int32_t bins) {
-  const double scale = (double)bins / range;
-  int32_t b;
-  if constexpr (kF64) {
-    const double f = floor(x * scale);
-    b = (f < 0.0) ? 0 : (f > (double)(bins - 1)) ? bins - 1 : (int32_t)f;
-  } else {
-    const float f = floorf(x * (float)scale);
-    b = (f < 0.0f) ? 0 : (f > (float)(bins - 1)) ? bins - 1 : (int32_t)f;
-  }
-  return b;
-}
-
 // ------------------------------------------------------------- the kernel
 
-template <bool kF64>
+template <int kMode>
 __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ SimArgs a) {
-  using R = std::conditional_t<kF64, double, float>;
+  using R = typename Types<kMode>::R;
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr bool kF64 = kMode == kModeF64;
   GraphView g = a.g;
   const int32_t hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
-  const SmemLayout lay = smem_layout(g.V, g.E, g.S, kF64, a.stage_smem, a.smem_counters, hist_len);
+  const SmemLayout lay = smem_layout(g.V, g.E, g.S, kF64, a.stage_smem, a.smem_counters,
+                                     hist_len, (int32_t)blockDim.x);
   if (a.stage_smem) {
     if constexpr (kF64) {
       block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
@@ -382,104 +461,106 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
   }
   uint32_t* shist = a.smem_hist ? reinterpret_cast<uint32_t*>(smem + lay.hist) : nullptr;
   if (shist) block_zero(shist, hist_len);
+  R* ring = reinterpret_cast<R*>(smem + lay.ring);
   __syncthreads();
 
-  ThreadCounters tc{0};
+  uint32_t trunc = 0;
   uint64_t psteps = 0;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t pid = a.pid_base + (uint32_t)i;
+  Lane<kMode> p;
+  p.active = false;
+  p.pending = false;
+  bool ok = false, alive0 = false;
   if (i < a.n) {
-    Particle<kF64> p;
     p.e = a.s.edge[i];
     p.x = reinterpret_cast<const R*>(a.s.x)[i];
+    p.n_draw = a.s.n_draw[i];
     p.hits = a.s.hits[i];
     p.first_hits = a.s.first_hits[i];
     p.flags = a.s.flags[i];
-    const uint32_t pid = a.pid_base + (uint32_t)i;
-    bool ok = p.e >= kDead && p.e < g.E;
+    ok = p.e >= kDead && p.e < g.E;
     if (!ok) atomicOr(a.c.err, kErrBadEdge);
     if (ok && p.e >= 0) {
-      load_edge<kF64>(g, p.e, a.dt, a.sqrt_dt, p.ed);
-      if (!(p.x >= (R)0 && p.x <= p.ed.L)) {
+      const R x0 = p.x;
+      enter_edge<kMode>(p, g, p.e, a);
+      p.x = x0;
+      if (!(p.x >= R(0) && p.x <= p.L)) {
         atomicOr(a.c.err, kErrNan);
         ok = false;
       }
-      p.at_v = (p.x == (R)0) || (p.x == p.ed.L);
     }
-    if (ok && p.e >= 0 && a.steps > 0) {
-      const uint64_t t0 = a.t_begin, t1 = a.t_begin + (uint64_t)a.steps;
-      uint64_t t = t0;
-      bool alive = true;
-      // head: steps up to the next multiple of four
-      if (t & 3u) {
-        const U4 w = philox4x32_10((uint32_t)(t >> 2), pid, 0u, a.instance, a.rk);
-        R z[4];
-        box_muller<kF64>(w.x, w.y, z[0], z[1]);
-        box_muller<kF64>(w.z, w.w, z[2], z[3]);
-#pragma unroll
-        for (int l = 1; l < 4; ++l) {
-          if (alive && (int)(t & 3u) == l && t < t1) {
-            alive = em_step<kF64>(p, z[l], a, g, bc, tc, pid);
-            if (alive) ++t;
-          }
-        }
+    alive0 = ok && p.e >= 0;
+    if (alive0 && a.steps > 0) {
+      p.active = true;
+      p.left = (uint32_t)a.steps;
+      p.k = 0;
+      p.in_cont = false;
+      use_step_coefficients(p, a);
+      p.at_v = (p.x == R(0)) || (p.x == p.L);
+      p.wand = 0xffffffffu;
+      p.wor = 0u;
+      p.cur_slot = -1;
+      if (p.at_v) {
+        const int32_t end = (p.x == R(0)) ? kEndInit : kEndTerm;
+        if constexpr (kF64) p.cur_slot = (end == kEndInit) ? g.e64[p.e].slot_init : g.e64[p.e].slot_term;
+        else p.cur_slot = (end == kEndInit) ? g.e32[p.e].slot_init : g.e32[p.e].slot_term;
+        set_vertex_sign(p, end);
       }
-      // body: whole groups of four steps share one Philox block
-      const uint64_t g_end = t1 >> 2;
-      for (uint64_t grp = t >> 2; alive && grp < g_end; ++grp) {
-        const U4 w = philox4x32_10((uint32_t)grp, pid, 0u, a.instance, a.rk);
-        R z0, z1, z2, z3;
-        box_muller<kF64>(w.x, w.y, z0, z1);
-        box_muller<kF64>(w.z, w.w, z2, z3);
-        t = grp << 2;
-        if (!(alive = em_step<kF64>(p, z0, a, g, bc, tc, pid))) break;
-        ++t;
-        if (!(alive = em_step<kF64>(p, z1, a, g, bc, tc, pid))) break;
-        ++t;
-        if (!(alive = em_step<kF64>(p, z2, a, g, bc, tc, pid))) break;
-        ++t;
-        if (!(alive = em_step<kF64>(p, z3, a, g, bc, tc, pid))) break;
-        t = (grp + 1) << 2;
-      }
-      // tail: the last t1 mod 4 steps
-      if (alive && t < t1) {
-        const U4 w = philox4x32_10((uint32_t)(t >> 2), pid, 0u, a.instance, a.rk);
-        R z[4];
-        box_muller<kF64>(w.x, w.y, z[0], z[1]);
-        box_muller<kF64>(w.z, w.w, z[2], z[3]);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          if (alive && (int)(t & 3u) == l && t < t1) {
-            alive = em_step<kF64>(p, z[l], a, g, bc, tc, pid);
-            if (alive) ++t;
-          }
-        }
-      }
-      // a particle absorbed during step t took steps t0 .. t
-      psteps = alive ? (uint64_t)a.steps : (t - t0 + 1);
+      p.n_gen = p.n_draw & ~3u;
+      refill<kMode>(p, ring, a, pid);
     }
-    if (ok) {
-      a.s.edge[i] = p.e;
-      reinterpret_cast<R*>(a.s.x)[i] = p.x;
-      a.s.hits[i] = p.hits;
-      a.s.first_hits[i] = p.first_hits;
-      a.s.flags[i] = p.flags;
-      // fused snapshot histogram of the final position
-      if (a.hist_bins > 0 && p.e >= 0) {
-        const int32_t bin = hist_bin<kF64>(p.x, g.range[p.e], a.hist_bins);
-        const int32_t key = p.e * a.hist_bins + bin;
-        if (shist) atomicAdd(&shist[key], 1u);
-        else atomicAdd(&a.hist[key], 1u);
-      }
+  }
+
+  // One sub-step per lane per iteration; pending vertex hits resolved in
+  // warp-wide batches (split_batch lanes, or whenever nothing else moves).
+  // Every iteration moves some lane forward, so the loop ends; the cap is a
+  // guard that turns a logic error into a reported fault instead of a hang.
+  const uint32_t full = 0xffffffffu;
+  const uint64_t cap = (uint64_t)a.steps * (uint64_t)(2 * a.M + 2) + 64;
+  uint64_t iters = 0;
+  for (;;) {
+    if (p.active && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
+    const uint32_t am = __ballot_sync(full, p.active);
+    if (am == 0u) break;
+    if (++iters > cap) {
+      if (p.active) atomicOr(a.c.err, kErrStuck);
+      break;
+    }
+    const uint32_t pm = __ballot_sync(full, p.pending);
+    if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
+      if (p.pending) split<kMode>(p, g, a, bc, pid, trunc);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (p.active && !p.pending) sub_step<kMode>(p, ring, a, bc);
+  }
+
+  if (ok && i < a.n) {
+    // steps taken while alive: an absorbed particle took the step it died in
+    if (alive0 && a.steps > 0)
+      psteps = (uint64_t)a.steps - p.left + ((p.e < 0) ? 1u : 0u);
+    a.s.edge[i] = p.e;
+    reinterpret_cast<R*>(a.s.x)[i] = p.x;
+    a.s.n_draw[i] = p.n_draw;
+    a.s.hits[i] = p.hits;
+    a.s.first_hits[i] = p.first_hits;
+    a.s.flags[i] = p.flags;
+    if (a.hist_bins > 0 && p.e >= 0) {
+      const int32_t bin = hist_bin<R>(p.x, g.range[p.e], a.hist_bins);
+      const int32_t key = p.e * a.hist_bins + bin;
+      if (shist) atomicAdd(&shist[key], 1u);
+      else atomicAdd(&a.hist[key], 1u);
     }
   }
 
   // per-warp reduction of the scalar counters
-  uint32_t tr = tc.trunc;
+  uint32_t tr = trunc;
   unsigned long long ps = psteps;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    tr += __shfl_down_sync(0xffffffffu, tr, off);
-    ps += __shfl_down_sync(0xffffffffu, ps, off);
+    tr += __shfl_down_sync(full, tr, off);
+    ps += __shfl_down_sync(full, ps, off);
   }
   if ((threadIdx.x & 31) == 0) {
     if (tr) atomicAdd(a.c.trunc, (unsigned long long)tr);
@@ -498,12 +579,11 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
 }
 
 // Snapshot histogram of the living particles (no stepping).
-template <bool kF64>
+template <typename R>
 __global__ void __launch_bounds__(256) histogram_kernel(GraphView g, const int32_t* __restrict__ edge,
                                                         const void* __restrict__ xv, int64_t n,
                                                         int32_t bins, uint32_t* __restrict__ out,
                                                         int32_t use_smem) {
-  using R = std::conditional_t<kF64, double, float>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
   const int32_t len = g.E * bins;
@@ -516,7 +596,7 @@ __global__ void __launch_bounds__(256) histogram_kernel(GraphView g, const int32
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = edge[i];
     if (e < 0 || e >= g.E) continue;
-    const int32_t key = e * bins + hist_bin<kF64>(x[i], g.range[e], bins);
+    const int32_t key = e * bins + hist_bin<R>(x[i], g.range[e], bins);
     if (use_smem) atomicAdd(&sh[key], 1u);
     else atomicAdd(&out[key], 1u);
   }

@@ -15,7 +15,9 @@ namespace mg {
 enum : int32_t { kEndInit = 0, kEndTerm = 1, kDead = -1 };
 enum : int32_t { kVertexStandard = 0, kVertexAbsorbing = 1 };
 // device-error bits (same values as MG_DEVERR_* in the public header)
-enum : uint32_t { kErrBadEdge = 1u, kErrNan = 2u };
+enum : uint32_t { kErrBadEdge = 1u, kErrNan = 2u, kErrStream = 4u, kErrStuck = 8u };
+// precision modes (same values as mg_precision)
+enum : int { kModeF64 = 0, kModeMixed = 1, kModeF32 = 2 };
 
 // One edge (Definition 1) with its drift mu_e(x) = c0 + c1 x and diffusion
 // sigma_e; 32 bytes so a warp loads it with one 16-byte pair per lane.
@@ -55,7 +57,8 @@ struct GraphView {
 // Particle state, structure of arrays.
 struct StateView {
   int32_t* edge;
-  void* x;  // float* (FP32 mixed) or double* (FP64)
+  void* x;  // float* (binary32 modes) or double* (binary64)
+  uint32_t* n_draw;  // normals used so far
   uint32_t* hits;
   uint32_t* first_hits;
   uint32_t* flags;
@@ -84,6 +87,7 @@ struct SimArgs {
   int32_t M;
   int32_t hist_bins;    // 0: no fused histogram
   uint32_t* hist;       // [E * hist_bins]
+  int32_t split_batch;  // pending lanes that trigger a batched split pass
   int32_t stage_smem;   // graph tables staged in shared memory
   int32_t smem_counters;// exit/absorbed counters privatised in shared memory
   int32_t smem_hist;    // histogram privatised in shared memory
@@ -92,15 +96,18 @@ struct SimArgs {
 // Dynamic shared memory of the fused kernel: staged tables, privatised
 // counters, privatised histogram (each part optional).
 struct SmemLayout {
-  size_t edges, slots, vtx, exits, absorbed, hist, total;
+  size_t ring, edges, slots, vtx, exits, absorbed, hist, total;
 };
 
 MG_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
-                                                  bool stage, bool counters, int32_t hist_len) {
+                                                  bool stage, bool counters, int32_t hist_len,
+                                                  int32_t block) {
   SmemLayout l{};
   size_t off = 0;
+  l.ring = off;  // 8 buffered normals per thread
+  off += align16((size_t)8 * block * (f64 ? 8 : 4));
   if (stage) {
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));

@@ -53,6 +53,7 @@ def assert_fp64_parity(gs, gc, o, *, max_flag_frac=0.01, ghist=None):
     ok = ~flagged
     assert flagged.mean() <= max_flag_frac, flagged.mean()
     assert np.array_equal(gs["edge"][ok], o["edge"][ok])
+    assert np.array_equal(gs["n_draw"][ok], o["n_draw"][ok])
     assert np.array_equal(gs["hits"][ok], o["hits"][ok])
     assert np.array_equal(gs["first_hits"][ok], o["first_hits"][ok])
     dx = np.abs(gs["x"][ok] - o["x"][ok])
@@ -153,9 +154,12 @@ def test_edge_cases_fp64(B):
 
 # ------------------------------------------------------------ invariances
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+MODES = {"fp64": 0, "mixed": 1, "fp32": 2}
+
+
+@pytest.mark.parametrize("prec", list(MODES))
 def test_chunking_sharding_resume_bit_exact(B, prec):
-    P = B.MG_FP64 if prec == "fp64" else B.MG_FP32_MIXED
+    P = MODES[prec]
     d = W.random_mixed(3)
     n = 6000
     e, x = W.uniform_on_edges(d, n, 4)
@@ -164,7 +168,7 @@ def test_chunking_sharding_resume_bit_exact(B, prec):
     b, cb, hb = gpu_run(B, d, e, x, steps=600, chunks=[200, 200, 200], bins=8, **kw)
     c, cc, hc = gpu_run(B, d, e, x, steps=600, chunks=[1, 598, 1], bins=8, **kw)
     for other, co, ho in [(b, cb, hb), (c, cc, hc)]:
-        for k in ("edge", "x", "hits", "first_hits", "flags"):
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
             assert np.array_equal(a[k], other[k]), k
         for k in ("exits", "absorbed"):
             assert np.array_equal(ca[k], co[k])
@@ -187,16 +191,38 @@ def test_chunking_sharding_resume_bit_exact(B, prec):
     q.simulate(3e-3, 350, 6)
     r = q.state()
     assert r["step"] == 600
-    for k in ("edge", "x", "hits", "first_hits", "flags"):
+    for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
         assert np.array_equal(a[k], r[k]), k
     p.close(); q.close(); g.close()
+
+
+@pytest.mark.parametrize("prec", list(MODES))
+def test_split_batching_does_not_change_results(B, prec):
+    """How many pending vertex hits a warp collects before resolving them is
+    a launch choice: every setting gives bit-identical results."""
+    d = W.star_langevin(16)
+    e, x = W.uniform_on_edges(d, 20_000, 2)
+    g = B.Graph(d)
+    outs = []
+    for sb in (1, 5, 32):
+        p = B.Particles(g, e, x, seed=3, precision=MODES[prec])
+        p.set_tuning(split_batch=sb)
+        p.simulate(2e-3, 300, 16)
+        p.synchronize()
+        outs.append((p.state(), p.counts()))
+        p.close()
+    g.close()
+    for st, cn in outs[1:]:
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+            assert np.array_equal(outs[0][0][k], st[k]), k
+        assert np.array_equal(outs[0][1]["exits"], cn["exits"])
 
 
 def test_fused_histogram_matches_standalone(B):
     import torch
     d = W.star_langevin(16)
     e, x = W.uniform_on_edges(d, 50_000, 1)
-    for P in (B.MG_FP32_MIXED, B.MG_FP64):
+    for P in (B.MG_FP32, B.MG_FP32_MIXED, B.MG_FP64):
         g = B.Graph(d)
         p = B.Particles(g, e, x, seed=4, precision=P)
         h = torch.zeros(16 * 32, dtype=torch.int32, device="cuda")
@@ -256,13 +282,14 @@ def _occupancy(edge, E):
     return np.bincount(edge[alive], minlength=E) / len(edge)
 
 
-def test_star16_langevin_fp32_statistics(B):
-    """FP32-mixed vs the FP64 oracle on the 16-edge Langevin star: same
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_star16_langevin_fp32_statistics(B, prec):
+    """binary32 modes vs the FP64 oracle on the 16-edge Langevin star: same
     streams, N = 2^16, 2000 steps."""
     d = W.star_langevin(16)
     n = 1 << 16
     e, x = W.uniform_on_edges(d, n, 11)
-    gs, gc, gh = gpu_run(B, d, e, x, seed=0, dt=1e-3, steps=2000, M=16, prec=B.MG_FP32_MIXED,
+    gs, gc, gh = gpu_run(B, d, e, x, seed=0, dt=1e-3, steps=2000, M=16, prec=MODES[prec],
                          bins=32)
     o = oracle_pool.run(d, e, x, seed=0, dt=1e-3, steps=2000, M=16, bins=32)
     po, pg = _occupancy(o["edge"], 16), _occupancy(gs["edge"], 16)
@@ -313,10 +340,11 @@ def test_star16_full_size_sampled(B):
     p.close()
     g.close()
     o64 = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=1e-3, steps=200, M=16)
-    sub = {k: s64[k][idx] for k in ("edge", "x", "hits", "first_hits", "flags")}
+    sub = {k: s64[k][idx] for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags")}
     flagged = ((sub["flags"] | o64["flags"]) & 1) != 0
     ok = ~flagged
     assert np.array_equal(sub["edge"][ok], o64["edge"][ok])
+    assert np.array_equal(sub["n_draw"][ok], o64["n_draw"][ok])
     assert np.all(np.abs(sub["x"][ok] - o64["x"][ok]) <= REL * np.maximum(1, np.abs(o64["x"][ok])))
 
 
