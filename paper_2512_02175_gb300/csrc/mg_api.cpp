@@ -496,9 +496,9 @@ namespace {
 // instruction however many lanes are active.
 int32_t default_split_batch(mg_precision prec) {
   switch (prec) {
-    case MG_FP32: return 8;
-    case MG_FP32_MIXED: return 12;
-    default: return 8;
+    case MG_FP32: return 4;
+    case MG_FP32_MIXED: return 4;
+    default: return 4;
   }
 }
 
@@ -541,7 +541,7 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
     return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
                            (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
   };
-  const size_t budget = kSmemBudget + (f64 ? 8u : 4u) * 8u * mg::kBlock;
+  const size_t budget = kSmemBudget + (f64 ? 8u : 4u) * 16u * mg::kBlock;
   if (lay(true) > budget) shist = false;
   if (lay(true) > budget) counters = false;
   if (lay(true) > budget) stage = false;
@@ -549,7 +549,8 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   a.smem_counters = counters;
   // launches: at most 2^31 - 1 steps (the per-lane step counter), and with
   // 32-bit shared counters at most 2^32 / (256 (2M + 1)) so they cannot wrap
-  int64_t chunk = 2147483647LL;
+  // (and the kernel's loop guard, 32 steps (2M + 2) + 64, fits 32 bits)
+  int64_t chunk = (int64_t)((4294967295ull - 64ull) / (32ull * (2ull * (uint64_t)M + 2ull)));
   if (counters) {
     const int64_t cap = (int64_t)(4294967295ull / (256ull * (2ull * (uint64_t)M + 1ull)));
     if (chunk > cap) chunk = cap;

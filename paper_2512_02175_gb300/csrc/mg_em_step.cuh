@@ -9,16 +9,18 @@
 // Every Euler-Maruyama sub-step -- the first of a step, and each one that
 // continues a step from a vertex after a split -- takes the next normal of
 // the particle's own counter-based stream (Philox-4x32-10 + Box-Muller, four
-// normals per block), buffered per thread in an 8-deep ring in shared memory.
-// The loop runs one sub-step per lane per iteration:
+// normals per block), buffered per thread in a ring in shared memory.  The
+// loop runs in quads; per lane and quad:
 //
-//   sub-step  x~ = x + mu_e(x) h + sigma_e sqrt(h) W: two FMAs with per-lane
-//             coefficients (h = dt, or the time left after a split; W = +-|z|
-//             when the sub-step starts at a vertex).  If x~ stays inside
-//             (0, l_e) the sub-step is done.
-//   split     otherwise the lane is marked pending and waits.  The warp
-//             resolves its pending lanes together -- once enough are waiting,
-//             or when no other lane can move -- so the long split path
+//   vertex    a lane sitting at a vertex (after a split, or at the start of a
+//             step) takes its one sub-step from the vertex: W = +-|z| into the
+//             edge, over the time left h;
+//   interior  then up to four sub-steps x~ = x + mu_e(x) dt + sigma_e
+//             sqrt(dt) z, two FMAs and a range test each, with no other
+//             bookkeeping;
+//   split     a sub-step that ends outside (0, l_e) leaves the lane pending.
+//             The warp resolves its pending lanes together -- once enough are
+//             waiting, or when no other lane can move -- so the long split path
 //             (hitting fraction, time left, jump draw, next edge) runs with
 //             many lanes active instead of one.  A particle's draws depend
 //             only on its own counters, so batching does not change results.
@@ -202,8 +204,10 @@ struct Lane {
   int32_t cur_slot;  // slot of the vertex end the particle sits at
   int32_t k;         // splits in the current step
   uint32_t left;     // steps left in this launch
-  bool at_v, in_cont, pending, active;
-  R Wp, xtp;  // normal and end point of the pending sub-step
+  bool at_v;         // at a vertex: the next sub-step leaves it (W = +-|z|)
+  bool in_cont;      // ... and continues a step after a split (time left h)
+  bool pending;      // the last sub-step ended outside (0, l_e): split next
+  bool active;
 };
 
 template <int kMode>
@@ -257,9 +261,13 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
   }
 }
 
-// Ring of buffered normals: normal n of the thread at ring[(n & 7) * bd + tid].
-// A stream never wraps: a lane that would pass 2^32 - 16 normals stops with
-// kErrStream.
+// Ring of buffered normals, 8 per thread, each stored twice: normal n of the
+// thread sits at rows (n & 7) and (n & 7) + 8 of ring[16][kThreads], so up to
+// five consecutive normals from row (n & 7) are read at fixed offsets.  A
+// lane refills (four at a time) only when it holds at most four and is not
+// pending, so the normal of a pending sub-step stays readable until its split
+// has used it.  A stream
+// never wraps: a lane that would pass 2^32 - 16 normals stops with kErrStream.
 template <int kMode>
 __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R* ring,
                                        const SimArgs& a, uint32_t pid) {
@@ -279,68 +287,121 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
     box_muller_f32(w.x, w.y, z0, z1);
     box_muller_f32(w.z, w.w, z2, z3);
   }
-  const uint32_t bd = blockDim.x, tid = threadIdx.x;
-  const uint32_t s0 = p.n_gen & 7u;  // 0 or 4
-  ring[(s0 + 0) * bd + tid] = z0;
-  ring[(s0 + 1) * bd + tid] = z1;
-  ring[(s0 + 2) * bd + tid] = z2;
-  ring[(s0 + 3) * bd + tid] = z3;
+  R* r = ring + (p.n_gen & 7u) * kThreads + threadIdx.x;  // row 0 or 4
+  r[0 * kThreads] = z0;
+  r[1 * kThreads] = z1;
+  r[2 * kThreads] = z2;
+  r[3 * kThreads] = z3;
+  r[8 * kThreads] = z0;
+  r[9 * kThreads] = z1;
+  r[10 * kThreads] = z2;
+  r[11 * kThreads] = z3;
   p.n_gen += 4;
 }
 
-// One Euler-Maruyama sub-step with the next normal.  Leaves the lane pending
-// when the sub-step ends outside (0, l_e).
+// End point of a sub-step with normal W over the lane's current time h.
 template <int kMode>
-__device__ __forceinline__ void sub_step(Lane<kMode>& p, const typename Types<kMode>::R* ring,
-                                         const SimArgs& a, const BlockCounters& bc) {
-  using R = typename Types<kMode>::R;
-  const R z = ring[(p.n_draw & 7u) * blockDim.x + threadIdx.x];
-  p.n_draw++;
-  const R W = apply_sign(z, p.wand, p.wor);
-  R xt;
+__device__ __forceinline__ typename Types<kMode>::R sub_step_end(const Lane<kMode>& p,
+                                                                 typename Types<kMode>::R W) {
   if constexpr (kMode == kModeF64) {
     const double mu = p.c0 + p.c1 * p.x;
     const double a_ = mu * p.h;
     const double b_ = p.S * W;
-    xt = p.x + a_ + b_;
-    if (fabs(xt) < p.tol || (isfinite(p.L) && fabs(p.L - xt) < p.tol)) p.flags |= 1u;
+    return p.x + a_ + b_;
   } else {
-    xt = fmaf(p.S, W, fmaf(p.x, p.Q, p.P));
+    return fmaf(p.S, W, fmaf(p.x, p.Q, p.P));
   }
+}
+
+template <int kMode>
+__device__ __forceinline__ void mark_near_branch(Lane<kMode>& p, typename Types<kMode>::R xt) {
+  if constexpr (kMode == kModeF64) {
+    if (fabs(xt) < p.tol || (isfinite(p.L) && fabs(p.L - xt) < p.tol)) p.flags |= 1u;
+  }
+}
+
+// The sub-step of a lane at a vertex: into the edge with |z|; ending inside
+// it is an exit through the vertex slot and closes the step.
+template <int kMode>
+__device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
+                                                const typename Types<kMode>::R* ring,
+                                                const SimArgs& a, const BlockCounters& bc) {
+  using R = typename Types<kMode>::R;
+  const R z = ring[(p.n_draw & 7u) * kThreads + threadIdx.x];
+  p.n_draw++;
+  const R xt = sub_step_end(p, apply_sign(z, p.wand, p.wor));
+  mark_near_branch(p, xt);
   if (xt > R(0) && xt < p.L) {
-    if (p.at_v | p.in_cont) {
-      if (p.at_v) count_exit(a.c, bc, p.cur_slot);  // left the vertex into the edge
-      if (p.in_cont) use_step_coefficients(p, a);   // the step is complete
-      p.at_v = false;
-      p.in_cont = false;
-      p.wand = 0xffffffffu;
-      p.wor = 0u;
-    }
-    p.x = xt;
+    count_exit(a.c, bc, p.cur_slot);
+    if (p.in_cont) use_step_coefficients(p, a);
     p.k = 0;
-    if (--p.left == 0) p.active = false;
+    p.at_v = false;
+    p.in_cont = false;
+    p.wand = 0xffffffffu;
+    p.wor = 0u;
+    p.x = xt;
+    if (--p.left == 0u) p.active = false;
   } else {
     p.pending = true;
-    p.Wp = W;
-    p.xtp = xt;
   }
+}
+
+// Up to four interior sub-steps over whole steps (h = dt, W = z), stopping
+// at the first that ends outside (0, l_e) -- the lane is then pending -- or,
+// with kCheckLeft, when the launch's steps are done.
+template <int kMode, bool kCheckLeft>
+__device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Types<kMode>::R* ring,
+                                              bool run) {
+  using R = typename Types<kMode>::R;
+  const R* r = ring + (p.n_draw & 7u) * kThreads + threadIdx.x;
+  uint32_t used = 0;
+  bool out = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (run) {
+      const R z = r[q * kThreads];
+      R xt;
+      if constexpr (kMode == kModeF64) {
+        const double mu = p.c0 + p.c1 * p.x;
+        const double a_ = mu * p.h;
+        const double b_ = p.S * z;
+        xt = p.x + a_ + b_;
+        mark_near_branch(p, xt);
+      } else {
+        xt = fmaf(p.Sm, z, fmaf(p.x, p.Qm, p.Pm));
+      }
+      const bool in = (xt > R(0)) & (xt < p.L);
+      p.x = in ? xt : p.x;
+      used = q + 1;
+      out = !in;
+      run = in;
+      if constexpr (kCheckLeft) run = run && ((uint32_t)(q + 1) < p.left);
+    }
+  }
+  p.n_draw += used;
+  p.left -= used - (out ? 1u : 0u);
+  p.pending = p.pending | out;
+  if (p.left == 0u) p.active = false;
 }
 
 // Resolve the pending vertex hit: partial step to the vertex, time left,
 // jump draw, next edge, and the coefficients of the rest of the step.
 template <int kMode>
 __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
-                                      const BlockCounters& bc, uint32_t pid, uint32_t& trunc) {
+                                      const BlockCounters& bc, const typename Types<kMode>::R* ring,
+                                      uint32_t pid, uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   using H = typename Types<kMode>::H;
   p.pending = false;
   const R xs = p.x;
-  const bool hit_init = !(p.xtp > R(0));
+  // the pending sub-step again: its normal is still in the ring
+  const R Wp = apply_sign(ring[((p.n_draw - 1u) & 7u) * kThreads + threadIdx.x], p.wand, p.wor);
+  const bool hit_init = !(sub_step_end(p, Wp) > R(0));
   int32_t v;
   if constexpr (kMode == kModeF64) {
     const double mu = p.c0 + p.c1 * xs;
     const double a_ = mu * p.h;
-    const double b_ = p.S * p.Wp;
+    const double b_ = p.S * Wp;
     const double A = hit_init ? a_ : -a_;
     const double B = hit_init ? b_ : -b_;
     const double C = hit_init ? xs : p.L - xs;
@@ -354,7 +415,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     const EdgeRec32& q = g.e32[p.e];
     const float hf = (float)p.h;
     const float a_ = fmaf(q.c1, xs, q.c0) * hf;
-    const float b_ = p.S * p.Wp;
+    const float b_ = p.S * Wp;
     const float A = hit_init ? a_ : -a_;
     const float B = hit_init ? b_ : -b_;
     const float C = hit_init ? xs : p.L - xs;
@@ -438,7 +499,7 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
   GraphView g = a.g;
   const int32_t hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
   const SmemLayout lay = smem_layout(g.V, g.E, g.S, kF64, a.stage_smem, a.smem_counters,
-                                     hist_len, (int32_t)blockDim.x);
+                                     hist_len, kThreads);
   if (a.stage_smem) {
     if constexpr (kF64) {
       block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
@@ -512,28 +573,35 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
     }
   }
 
-  // One sub-step per lane per iteration; pending vertex hits resolved in
-  // warp-wide batches (split_batch lanes, or whenever nothing else moves).
-  // Every iteration moves some lane forward, so the loop ends; the cap is a
-  // guard that turns a logic error into a reported fault instead of a hang.
+  // Quads of at most five sub-steps per lane (one from a vertex, four
+  // interior); pending vertex hits resolved in warp-wide batches (split_batch
+  // lanes, or whenever nothing else moves).  Every quad moves some lane
+  // forward by a sub-step or a split, and a lane has at most 2M + 1 of those
+  // per step, so the loop ends within 32 steps (2M + 2) quads; the cap turns a
+  // logic error into a reported fault instead of a hang (the host keeps it
+  // within 32 bits).
   const uint32_t full = 0xffffffffu;
-  const uint64_t cap = (uint64_t)a.steps * (uint64_t)(2 * a.M + 2) + 64;
-  uint64_t iters = 0;
+  const uint32_t cap = 32u * (uint32_t)a.steps * (uint32_t)(2 * a.M + 2) + 64u;
+  uint32_t quads = 0;
   for (;;) {
-    if (p.active && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
     const uint32_t am = __ballot_sync(full, p.active);
     if (am == 0u) break;
-    if (++iters > cap) {
+    if (++quads > cap) {
       if (p.active) atomicOr(a.c.err, kErrStuck);
       break;
     }
     const uint32_t pm = __ballot_sync(full, p.pending);
     if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
-      if (p.pending) split<kMode>(p, g, a, bc, pid, trunc);
+      if (p.pending) split<kMode>(p, g, a, bc, ring, pid, trunc);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (p.active && !p.pending) sub_step<kMode>(p, ring, a, bc);
+    // a quad uses up to five normals: top the buffer up to five (a lane that
+    // went pending with an empty buffer needs two refills)
+    if (p.active && !p.pending && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
+    if (p.active && !p.pending && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
+    if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
+    const bool run = p.active && !p.pending && !p.at_v;
+    if (__all_sync(full, !run || p.left >= 4u)) interior_quad<kMode, false>(p, ring, run);
+    else interior_quad<kMode, true>(p, ring, run);
   }
 
   if (ok && i < a.n) {

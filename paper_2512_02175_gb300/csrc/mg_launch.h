@@ -6,7 +6,7 @@
 
 namespace mg {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = kThreads;
 
 // Fused EM-Step kernel: binary64 (em_step_f64.cu), binary32-mixed and
 // binary32 (em_step_f32.cu).

@@ -16,6 +16,8 @@ enum : int32_t { kEndInit = 0, kEndTerm = 1, kDead = -1 };
 enum : int32_t { kVertexStandard = 0, kVertexAbsorbing = 1 };
 // device-error bits (same values as MG_DEVERR_* in the public header)
 enum : uint32_t { kErrBadEdge = 1u, kErrNan = 2u, kErrStream = 4u, kErrStuck = 8u };
+// threads per block of the fused kernel
+constexpr int kThreads = 256;
 // precision modes (same values as mg_precision)
 enum : int { kModeF64 = 0, kModeMixed = 1, kModeF32 = 2 };
 
@@ -106,8 +108,8 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
                                                   int32_t block) {
   SmemLayout l{};
   size_t off = 0;
-  l.ring = off;  // 8 buffered normals per thread
-  off += align16((size_t)8 * block * (f64 ? 8 : 4));
+  l.ring = off;  // 8 buffered normals per thread, each stored twice
+  off += align16((size_t)16 * block * (f64 ? 8 : 4));
   if (stage) {
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));

@@ -329,9 +329,11 @@ def test_star16_full_size_sampled(B):
     o = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=1e-3, steps=10_000, M=16)
     same = st["edge"][idx] == o["edge"]
     assert same.mean() > 0.85, same.mean()
+    # occupancy of the whole population (N = 2^24: its own error is negligible)
+    # against the oracle's sample of 1024; 16 edges, so 4 standard errors
     po = _occupancy(o["edge"], 16)
     pg = np.bincount(st["edge"], minlength=16) / n
-    assert np.all(np.abs(pg - po) <= 3 * np.sqrt(po * (1 - po) / len(idx)) + 1e-9)
+    assert np.all(np.abs(pg - po) <= 4 * np.sqrt(pg * (1 - pg) / len(idx)) + 1e-9)
     # FP64 at full N: sampled trajectories exact
     p = B.Particles(g, e, x, seed=0, precision=B.MG_FP64)
     p.simulate(1e-3, 200, 16)
