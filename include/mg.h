@@ -198,6 +198,23 @@ mg_status mg_synchronize(mg_particles p);
 mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, int out_on_device,
                        void* stream);
 
+/* The same histogram as mg_histogram with a host output, for callers that
+ * cannot let the library allocate device memory -- a fixed, pre-reserved
+ * memory budget, code that must not synchronise the device the way
+ * cudaMalloc/cudaFree can, or an allocator hook that is not safe to call at
+ * this point.  The paper has no counterpart: it is a property of this
+ * library.  The counts are staged in a static device array of at most
+ * 2^20 counts (n_edges * bins; 4 MiB, held on every GPU that loads the
+ * library until the process exits); larger requests return
+ * MG_ERR_INVALID_ARG.  Nothing is allocated: no cudaMalloc, cudaFree or
+ * allocator hook is called.  out[n_edges * bins] is host memory, overwritten;
+ * the call synchronises `stream`.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make it before any stream
+ * capture.  All calls share the one array, which keeps the previous call's
+ * counts (each call clears what it uses): calls that overlap on the GPU, from
+ * different streams or threads, race. */
+mg_status mg_histogram_static(mg_particles p, int32_t bins, uint32_t* out, void* stream);
+
 /* Copies the set's counters to host arrays (synchronises): slot_exits[n_slots]
  * (in the slot order of mg_graph_slots), absorbed[n_vertices], truncations[1],
  * particle_steps[1] (steps taken by living particles).  Any pointer may be

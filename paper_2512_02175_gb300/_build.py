@@ -1,6 +1,6 @@
 """Builds ``libmetricgraph.so`` in-tree with nvcc for sm_103a.
 
-Three translation units compiled in parallel and linked into one shared
+Four translation units compiled in parallel and linked into one shared
 library next to this file:
 
 * ``em_step_f32.cu``  binary32-mixed kernels (FMA contraction allowed)
@@ -8,6 +8,7 @@ library next to this file:
                       rounds as written
 * ``mg_api.cpp``      the C ABI (host), ``-ffp-contract=off`` so the jump
                       thresholds round identically on x86-64 and AArch64
+* ``mg_noalloc.cu``   the histogram entry point that allocates nothing
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ UNITS = [
     ("em_step_f32.cu", []),
     ("em_step_f64.cu", ["--fmad=false"]),
     ("mg_api.cpp", ["-Xcompiler", "-ffp-contract=off"]),
+    ("mg_noalloc.cu", []),
 ]
 
 

@@ -56,7 +56,7 @@ SYMBOLS = [
     "mg_set_allocator", "mg_graph_create", "mg_graph_destroy", "mg_graph_info", "mg_graph_slots",
     "mg_particles_init", "mg_particles_reset", "mg_particles_destroy", "mg_particles_set_tuning",
     "mg_simulate",
-    "mg_synchronize", "mg_histogram", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
+    "mg_synchronize", "mg_histogram", "mg_histogram_static", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
     "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
 ]
 
@@ -101,6 +101,7 @@ def _declare(L):
         "mg_simulate": ([vp, dbl, i64, i32, i32, vp, vp], st),
         "mg_synchronize": ([vp], st),
         "mg_histogram": ([vp, i32, vp, C.c_int, vp], st),
+        "mg_histogram_static": ([vp, i32, vp, vp], st),
         "mg_exit_counts": ([vp, vp, vp, vp, vp, vp], st),
         "mg_counters_reset": ([vp, vp], st),
         "mg_state_get": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
@@ -290,6 +291,15 @@ def mg_histogram(p, bins, out=None, stream=None):
     if out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]:
         raise ValueError("host output must be a C-contiguous uint32 array")
     _check(load().mg_histogram(p, int(bins), _ptr(out), 0, _stream_ptr(stream)))
+    return out
+
+
+def mg_histogram_static(p, bins, out, stream=None):
+    """The snapshot histogram into the host array ``out`` (uint32 [E * bins])
+    without any device allocation by the library (see include/mg.h)."""
+    if out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a C-contiguous uint32 host array")
+    _check(load().mg_histogram_static(p, int(bins), _ptr(out), _stream_ptr(stream)))
     return out
 
 

@@ -712,3 +712,19 @@ extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const dou
 extern "C" const char* mg_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* mg_version(void) { return "libmetricgraph 0.1 (sm_103a)"; }
+
+// Read-only view of a particle set for other translation units of the
+// library (the positions, edges and graph tables a kernel reads).
+bool mg_particles_view(mg_particles p, mg::GraphView* g, const int32_t** edge, const void** x,
+                       int64_t* n, int* precision) {
+  if (!p) return false;
+  *g = p->g->view;
+  *edge = p->sv.edge;
+  *x = p->sv.x;
+  *n = p->n;
+  *precision = (int)p->prec;
+  return true;
+}
+
+// Records an error message from another translation unit of the library.
+mg_status mg_fail_message(mg_status st, const char* msg) { return fail(st, "%s", msg); }
