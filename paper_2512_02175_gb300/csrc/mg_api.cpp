@@ -491,14 +491,15 @@ extern "C" mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch
 
 namespace {
 
-// Default number of pending lanes that triggers a batched split pass: larger
-// where the split path carries binary64 work, which costs the same per warp
-// instruction however many lanes are active.
+// Default number of pending lanes that triggers a batched split pass.  With
+// eight interior sub-steps per loop iteration the pending lanes of one
+// iteration already form the batch; waiting for more costs more than it saves
+// (measured on the 16-edge Langevin star: 1 and 2 best, 8 about 20% slower).
 int32_t default_split_batch(mg_precision prec) {
   switch (prec) {
-    case MG_FP32: return 4;
-    case MG_FP32_MIXED: return 4;
-    default: return 4;
+    case MG_FP32: return 1;
+    case MG_FP32_MIXED: return 1;
+    default: return 1;
   }
 }
 
@@ -541,7 +542,7 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
     return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
                            (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
   };
-  const size_t budget = kSmemBudget + (f64 ? 8u : 4u) * 16u * mg::kBlock;
+  const size_t budget = kSmemBudget + 128u * mg::kBlock;  // + the normal ring
   if (lay(true) > budget) shist = false;
   if (lay(true) > budget) counters = false;
   if (lay(true) > budget) stage = false;

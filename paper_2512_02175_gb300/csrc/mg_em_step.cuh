@@ -90,12 +90,12 @@ __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double&
 }
 
 // binary32: u = (2 (w >> 9) + 1) 2^-24, formed exactly from the top 23 bits
-// (1 + m 2^-23 minus 1 - 2^-24), so the binary32 and binary64 modes see the
-// same words.  cos(2 pi u) = -cos(2 pi u - pi) keeps the hardware
+// (1 + m 2^-23 minus 1 - 2^-24; m < 2^23, so adding the exponent bits is an
+// OR), so the binary32 and binary64 modes see the same words.  cos(2 pi u) = -cos(2 pi u - pi) keeps the hardware
 // sine/cosine on (-pi, pi).  lg2/sqrt/sin/cos are the approximate hardware
 // instructions.
 __device__ __forceinline__ float u01_f32(uint32_t w) {
-  return __uint_as_float((w >> 9) | 0x3f800000u) - 0.99999994f;
+  return __uint_as_float((w >> 9) + 0x3f800000u) - 0.99999994f;
 }
 __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& zc, float& zs) {
   const float ua = u01_f32(wa), ub = u01_f32(wb);
@@ -135,6 +135,28 @@ __device__ __forceinline__ T hit_root(T A, T B, T C) {
   return s;
 }
 
+// The same root in binary32 with the hardware's approximate reciprocal and
+// square root (a few ulp; the result is clamped to [0, 1] all the same).
+__device__ __forceinline__ float hit_root_fast(float A, float B, float C) {
+  float s;
+  if (A == 0.0f) {
+    s = (B == 0.0f) ? 0.0f : __fdividef(-C, B);
+  } else {
+    const float disc = fmaf(B, B, -4.0f * A * C);
+    float d;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(d) : "f"(fmaxf(disc, 0.0f)));
+    if (B > 0.0f) {
+      s = __fdividef(-B - d, 2.0f * A);
+    } else {
+      const float den = -B + d;
+      s = (den == 0.0f) ? 0.0f : __fdividef(2.0f * C, den);
+    }
+  }
+  if (!(s > 0.0f)) s = 0.0f;
+  if (s > 1.0f) s = 1.0f;
+  return s;
+}
+
 // Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j
 // (thresholds are non-decreasing and the last is 2^32 > u).
 __device__ __forceinline__ int32_t choose_slot(const GraphView& g, const VtxRec& vr, uint32_t u) {
@@ -169,6 +191,10 @@ template <int kMode>
 struct Types {
   using R = std::conditional_t<kMode == kModeF64, double, float>;  // positions, normals
   using H = std::conditional_t<kMode == kModeF32, float, double>;  // alpha, time left
+  // interior sub-steps per loop iteration, and the ring of buffered normals:
+  // kRing per thread, each stored twice (rows n % kRing and n % kRing + kRing)
+  static constexpr int kSub = (kMode == kModeF64) ? 4 : 8;
+  static constexpr uint32_t kRing = 2 * kSub;
 };
 
 // Sign handling of the normal of a sub-step: W = (z & wand) | wor on the sign
@@ -255,19 +281,21 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
   } else {
     const EdgeRec32& q = g.e32[p.e];
     const float hf = (float)p.h;
+    float rh;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(hf));
     p.P = q.c0 * hf;
     p.Q = fmaf(q.c1, hf, 1.0f);
-    p.S = q.sigma * sqrtf(hf);
+    p.S = q.sigma * rh;
   }
 }
 
-// Ring of buffered normals, 8 per thread, each stored twice: normal n of the
-// thread sits at rows (n & 7) and (n & 7) + 8 of ring[16][kThreads], so up to
-// five consecutive normals from row (n & 7) are read at fixed offsets.  A
-// lane refills (four at a time) only when it holds at most four and is not
-// pending, so the normal of a pending sub-step stays readable until its split
-// has used it.  A stream
-// never wraps: a lane that would pass 2^32 - 16 normals stops with kErrStream.
+// Ring of buffered normals, kRing per thread, each stored twice: normal n of
+// the thread sits at rows n % kRing and n % kRing + kRing of
+// ring[2 kRing][kThreads], so kSub + 1 consecutive normals from row n % kRing
+// are read at fixed offsets.  A lane refills (four at a time) only while it
+// holds at most kSub and is not pending, so the normal of a pending sub-step
+// stays readable until its split has used it.  A stream never wraps: a lane
+// that would pass 2^32 - 16 normals stops with kErrStream.
 template <int kMode>
 __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R* ring,
                                        const SimArgs& a, uint32_t pid) {
@@ -287,15 +315,16 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
     box_muller_f32(w.x, w.y, z0, z1);
     box_muller_f32(w.z, w.w, z2, z3);
   }
-  R* r = ring + (p.n_gen & 7u) * kThreads + threadIdx.x;  // row 0 or 4
+  constexpr uint32_t K = Types<kMode>::kRing;
+  R* r = ring + (p.n_gen & (K - 1u)) * kThreads + threadIdx.x;  // a multiple of 4
   r[0 * kThreads] = z0;
   r[1 * kThreads] = z1;
   r[2 * kThreads] = z2;
   r[3 * kThreads] = z3;
-  r[8 * kThreads] = z0;
-  r[9 * kThreads] = z1;
-  r[10 * kThreads] = z2;
-  r[11 * kThreads] = z3;
+  r[(K + 0) * kThreads] = z0;
+  r[(K + 1) * kThreads] = z1;
+  r[(K + 2) * kThreads] = z2;
+  r[(K + 3) * kThreads] = z3;
   p.n_gen += 4;
 }
 
@@ -327,7 +356,7 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
                                                 const typename Types<kMode>::R* ring,
                                                 const SimArgs& a, const BlockCounters& bc) {
   using R = typename Types<kMode>::R;
-  const R z = ring[(p.n_draw & 7u) * kThreads + threadIdx.x];
+  const R z = ring[(p.n_draw & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x];
   p.n_draw++;
   const R xt = sub_step_end(p, apply_sign(z, p.wand, p.wor));
   mark_near_branch(p, xt);
@@ -346,18 +375,18 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
   }
 }
 
-// Up to four interior sub-steps over whole steps (h = dt, W = z), stopping
+// Up to kSub interior sub-steps over whole steps (h = dt, W = z), stopping
 // at the first that ends outside (0, l_e) -- the lane is then pending -- or,
 // with kCheckLeft, when the launch's steps are done.
 template <int kMode, bool kCheckLeft>
 __device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Types<kMode>::R* ring,
                                               bool run) {
   using R = typename Types<kMode>::R;
-  const R* r = ring + (p.n_draw & 7u) * kThreads + threadIdx.x;
+  const R* r = ring + (p.n_draw & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x;
   uint32_t used = 0;
   bool out = false;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < Types<kMode>::kSub; ++q) {
     if (run) {
       const R z = r[q * kThreads];
       R xt;
@@ -395,7 +424,9 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   p.pending = false;
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
-  const R Wp = apply_sign(ring[((p.n_draw - 1u) & 7u) * kThreads + threadIdx.x], p.wand, p.wor);
+  const R Wp = apply_sign(
+      ring[((p.n_draw - 1u) & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x], p.wand,
+      p.wor);
   const bool hit_init = !(sub_step_end(p, Wp) > R(0));
   int32_t v;
   if constexpr (kMode == kModeF64) {
@@ -419,7 +450,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     const float A = hit_init ? a_ : -a_;
     const float B = hit_init ? b_ : -b_;
     const float C = hit_init ? xs : p.L - xs;
-    const float s = hit_root<float>(A, B, C);
+    const float s = hit_root_fast(A, B, C);
     if constexpr (kMode == kModeMixed) {
       const double sd = (double)s;
       const double alpha = sd * sd;   // binary64 hitting fraction
@@ -573,8 +604,8 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
     }
   }
 
-  // Quads of at most five sub-steps per lane (one from a vertex, four
-  // interior); pending vertex hits resolved in warp-wide batches (split_batch
+  // Iterations of at most kSub + 1 sub-steps per lane (one from a vertex,
+  // kSub interior); pending vertex hits resolved in warp-wide batches (split_batch
   // lanes, or whenever nothing else moves).  Every quad moves some lane
   // forward by a sub-step or a split, and a lane has at most 2M + 1 of those
   // per step, so the loop ends within 32 steps (2M + 2) quads; the cap turns a
@@ -594,13 +625,15 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
     if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
       if (p.pending) split<kMode>(p, g, a, bc, ring, pid, trunc);
     }
-    // a quad uses up to five normals: top the buffer up to five (a lane that
-    // went pending with an empty buffer needs two refills)
-    if (p.active && !p.pending && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
-    if (p.active && !p.pending && p.n_gen - p.n_draw <= 4u) refill<kMode>(p, ring, a, pid);
+    // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
+    // lane that went pending with an empty buffer needs up to three refills)
+    constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
+#pragma unroll
+    for (int f = 0; f < (int)(kSub + 4) / 4; ++f)
+      if (p.active && !p.pending && p.n_gen - p.n_draw <= kSub) refill<kMode>(p, ring, a, pid);
     if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
     const bool run = p.active && !p.pending && !p.at_v;
-    if (__all_sync(full, !run || p.left >= 4u)) interior_quad<kMode, false>(p, ring, run);
+    if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
     else interior_quad<kMode, true>(p, ring, run);
   }
 

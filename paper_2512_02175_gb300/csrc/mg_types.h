@@ -108,8 +108,8 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
                                                   int32_t block) {
   SmemLayout l{};
   size_t off = 0;
-  l.ring = off;  // 8 buffered normals per thread, each stored twice
-  off += align16((size_t)16 * block * (f64 ? 8 : 4));
+  l.ring = off;  // buffered normals, each stored twice: 32 KB at 256 threads
+  off += align16((size_t)(f64 ? 16 : 32) * block * (f64 ? 8 : 4));
   if (stage) {
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));
