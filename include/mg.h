@@ -185,6 +185,48 @@ mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t s
 mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
                       int32_t hist_bins, uint32_t* hist_out, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ *
+ * A batch advances many particle sets (instances: different graphs, sizes,
+ * dt, step counts, M) in one launch of a persistent kernel: its blocks pop
+ * work items -- 256 particles of one instance -- from a queue ordered by
+ * decreasing step count, and run on each the same per-particle code as
+ * mg_simulate, so every particle's result is bit-identical alone and in any
+ * batch.  Members share one seed and one precision (instances differ by
+ * instance_id and pid); a member must stay alive while the batch uses it. */
+typedef struct mg_batch_s* mg_batch;
+
+mg_status mg_batch_create(mg_batch* out);
+
+/* Adds particle set p, to be advanced by `steps` EM-Steps of length dt with at
+ * most max_splits_M splits per step, optionally adding its final-position
+ * histogram to hist_out (device, [n_edges * hist_bins]), as mg_simulate does.
+ * MG_ERR_INVALID_ARG for a different seed or precision than the first
+ * member's, a set added twice, or the step arguments mg_simulate rejects. */
+mg_status mg_batch_add(mg_batch b, mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
+                       int32_t hist_bins, uint32_t* hist_out);
+
+mg_status mg_batch_clear(mg_batch b);
+
+/* Launch tuning (the results do not depend on it): split_batch as in
+ * mg_particles_set_tuning (0: default), stage_limit_bytes: a member's graph
+ * tables are staged in shared memory only when they take at most this many
+ * bytes (< 0: whenever they fit), blocks_per_sm: resident blocks of the
+ * persistent kernel per SM (0: the occupancy maximum). */
+mg_status mg_batch_set_tuning(mg_batch b, int32_t split_batch, int64_t stage_limit_bytes,
+                              int32_t blocks_per_sm);
+
+/* Advances every member once (stream-ordered).  The first run after a
+ * change builds the instance table and work queue in device memory; with
+ * use_graph != 0 it also captures the launch into a CUDA graph on `stream`
+ * (which must not be the legacy default stream) and later runs replay it. */
+mg_status mg_batch_run(mg_batch b, int use_graph, void* stream);
+
+/* Members, work items and persistent blocks of the last build. */
+mg_status mg_batch_info(mg_batch b, int32_t* n_members, int32_t* n_items, int32_t* blocks);
+
+mg_status mg_batch_destroy(mg_batch b);
+
 /* Waits for the set's stream work and reports any device-error bits as
  * MG_ERR_DEVICE_FAULT (the bits are in mg_last_error's message and are
  * cleared). */

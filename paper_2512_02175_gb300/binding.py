@@ -58,6 +58,8 @@ SYMBOLS = [
     "mg_simulate",
     "mg_synchronize", "mg_histogram", "mg_histogram_static", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
     "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
+    "mg_batch_create", "mg_batch_add", "mg_batch_clear", "mg_batch_set_tuning", "mg_batch_run",
+    "mg_batch_info", "mg_batch_destroy",
 ]
 
 _lock = threading.Lock()
@@ -107,6 +109,13 @@ def _declare(L):
         "mg_state_get": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
         "mg_state_set": ([vp, vp, vp, vp, vp, vp, vp, u64, vp], st),
         "mg_particles_info": ([vp, vp, vp, vp], st),
+        "mg_batch_create": ([C.POINTER(vp)], st),
+        "mg_batch_add": ([vp, vp, dbl, i64, i32, i32, vp], st),
+        "mg_batch_clear": ([vp], st),
+        "mg_batch_set_tuning": ([vp, i32, i64, i32], st),
+        "mg_batch_run": ([vp, C.c_int, vp], st),
+        "mg_batch_info": ([vp, vp, vp, vp], st),
+        "mg_batch_destroy": ([vp], st),
         "mg_last_error": ([], C.c_char_p),
         "mg_version": ([], C.c_char_p),
     }
@@ -337,6 +346,78 @@ def mg_state_set(p, state, stream=None):
     _check(load().mg_state_set(p, _ptr(a["edge"]), _ptr(a["x"]), _ptr(a["n_draw"]), _ptr(a["hits"]),
                                _ptr(a["first_hits"]), _ptr(a["flags"]), int(state["step"]),
                                _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------- batches
+
+def mg_batch_create():
+    h = C.c_void_p()
+    _check(load().mg_batch_create(C.byref(h)))
+    return h
+
+
+def mg_batch_add(b, p, dt, steps, M, hist_bins=0, hist_out=None):
+    _check(load().mg_batch_add(b, p, float(dt), int(steps), int(M), int(hist_bins),
+                               _ptr(hist_out)))
+
+
+def mg_batch_clear(b):
+    _check(load().mg_batch_clear(b))
+
+
+def mg_batch_set_tuning(b, split_batch=0, stage_limit_bytes=-1, blocks_per_sm=0):
+    _check(load().mg_batch_set_tuning(b, int(split_batch), int(stage_limit_bytes),
+                                      int(blocks_per_sm)))
+
+
+def mg_batch_run(b, use_graph=False, stream=None):
+    _check(load().mg_batch_run(b, int(bool(use_graph)), _stream_ptr(stream)))
+
+
+def mg_batch_info(b):
+    m, it, bl = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().mg_batch_info(b, C.byref(m), C.byref(it), C.byref(bl)))
+    return m.value, it.value, bl.value
+
+
+def mg_batch_destroy(b):
+    _check(load().mg_batch_destroy(b))
+
+
+class Batch:
+    """Owns an mg_batch handle; keeps its members (Particles) alive."""
+
+    def __init__(self):
+        self.h = mg_batch_create()
+        self.members = []
+
+    def add(self, parts, dt, steps, M, hist_bins=0, hist_out=None):
+        mg_batch_add(self.h, parts.h, dt, steps, M, hist_bins, hist_out)
+        self.members.append((parts, hist_out))
+
+    def clear(self):
+        mg_batch_clear(self.h)
+        self.members = []
+
+    def set_tuning(self, split_batch=0, stage_limit_bytes=-1, blocks_per_sm=0):
+        mg_batch_set_tuning(self.h, split_batch, stage_limit_bytes, blocks_per_sm)
+
+    def run(self, use_graph=False, stream=None):
+        mg_batch_run(self.h, use_graph, stream)
+
+    def info(self):
+        return mg_batch_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            mg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mg_version() -> str:

@@ -7,23 +7,71 @@
 namespace mg {
 
 template <int kMode>
-static cudaError_t launch_em(const SimArgs& a, size_t smem, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+static void set_smem_attributes() {
+  static bool done = false;
+  if (!done) {
     cudaFuncSetAttribute(em_step_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    attr = true;
+    cudaFuncSetAttribute(em_batch_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    done = true;
   }
+}
+
+cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
+                                cudaStream_t st) {
   const int64_t grid = (a.n + kBlock - 1) / kBlock;
-  em_step_kernel<kMode><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  if (mode == kModeMixed) {
+    set_smem_attributes<kModeMixed>();
+    em_step_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+  } else {
+    set_smem_attributes<kModeF32>();
+    em_step_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_em_step_mixed(const SimArgs& a, size_t smem, cudaStream_t st) {
-  return launch_em<kModeMixed>(a, smem, st);
+cudaError_t launch_em_batch_f32x(int mode, const SimArgs* insts, const BatchItem* items,
+                                 int32_t n_items, uint32_t* head, const Keys& k, size_t smem,
+                                 int blocks, cudaStream_t st) {
+  if (mode == kModeMixed) {
+    set_smem_attributes<kModeMixed>();
+    em_batch_kernel<kModeMixed><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
+  } else {
+    set_smem_attributes<kModeF32>();
+    em_batch_kernel<kModeF32><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
+  }
+  return cudaGetLastError();
 }
-cudaError_t launch_em_step_f32(const SimArgs& a, size_t smem, cudaStream_t st) {
-  return launch_em<kModeF32>(a, smem, st);
+
+int em_batch_blocks_per_sm_f32x(int mode, size_t smem) {
+  int nb = 0;
+  if (mode == kModeMixed) {
+    set_smem_attributes<kModeMixed>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeMixed>, kBlock, smem);
+  } else {
+    set_smem_attributes<kModeF32>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeF32>, kBlock, smem);
+  }
+  return nb;
+}
+
+cudaError_t launch_em_step(int mode, const SimArgs& a, const Keys& k, size_t smem,
+                           cudaStream_t st) {
+  return mode == kModeF64 ? launch_em_step_f64(a, k, smem, st)
+                          : launch_em_step_f32x(mode, a, k, smem, st);
+}
+
+cudaError_t launch_em_batch(int mode, const SimArgs* insts, const BatchItem* items, int32_t n_items,
+                            uint32_t* head, const Keys& k, size_t smem, int blocks,
+                            cudaStream_t st) {
+  return mode == kModeF64 ? launch_em_batch_f64(insts, items, n_items, head, k, smem, blocks, st)
+                          : launch_em_batch_f32x(mode, insts, items, n_items, head, k, smem,
+                                                 blocks, st);
+}
+
+int em_batch_blocks_per_sm(int mode, size_t smem) {
+  return mode == kModeF64 ? em_batch_blocks_per_sm_f64(smem) : em_batch_blocks_per_sm_f32x(mode, smem);
 }
 
 cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const void* x, int64_t n,

@@ -7,16 +7,37 @@
 
 namespace mg {
 
-cudaError_t launch_em_step_f64(const SimArgs& a, size_t smem, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+static void set_smem_attributes() {
+  static bool done = false;
+  if (!done) {
     cudaFuncSetAttribute(em_step_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    attr = true;
+    cudaFuncSetAttribute(em_batch_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    done = true;
   }
+}
+
+cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cudaStream_t st) {
+  set_smem_attributes();
   const int64_t grid = (a.n + kBlock - 1) / kBlock;
-  em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
   return cudaGetLastError();
+}
+
+cudaError_t launch_em_batch_f64(const SimArgs* insts, const BatchItem* items, int32_t n_items,
+                                uint32_t* head, const Keys& k, size_t smem, int blocks,
+                                cudaStream_t st) {
+  set_smem_attributes();
+  em_batch_kernel<kModeF64><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
+  return cudaGetLastError();
+}
+
+int em_batch_blocks_per_sm_f64(size_t smem) {
+  set_smem_attributes();
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeF64>, kBlock, smem);
+  return nb;
 }
 
 cudaError_t launch_histogram_f64(const GraphView& g, const int32_t* edge, const void* x, int64_t n,

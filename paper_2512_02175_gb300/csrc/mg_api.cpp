@@ -2,6 +2,7 @@
 // validation, graph tables, particle-set memory and kernel launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -505,79 +506,326 @@ int32_t default_split_batch(mg_precision prec) {
 
 }  // namespace
 
-extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t M,
-                                 int32_t hist_bins, uint32_t* hist_out, void* stream) {
-  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_simulate: NULL particles");
-  if (!(std::isfinite(dt) && dt > 0.0)) return fail(MG_ERR_INVALID_ARG, "dt must be finite and > 0");
-  if (steps < 0) return fail(MG_ERR_INVALID_ARG, "steps must be >= 0");
-  if (M < 1 || M > 1024) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be in [1, 1024]");
-  if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");
-  if (hist_bins > 0 && !hist_out) return fail(MG_ERR_INVALID_ARG, "hist_bins > 0 needs hist_out");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const mg_graph g = p->g;
-  const bool f64 = p->prec == MG_FP64;
+namespace {
 
+mg::Keys keys_of(uint64_t seed) {
+  mg::Keys k{};
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {
+    k.rk[2 * r] = k0 + r * 0x9E3779B9u;
+    k.rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
+  }
+  return k;
+}
+
+// Per-set launch arguments and shared-memory plan: the normal ring always;
+// then the tables (when their size is at most stage_limit), the counters and
+// the histogram, as long as the total stays within the budget.
+struct Plan {
   mg::SimArgs a{};
+  bool f64 = false, stage = true, counters = true, shist = false;
+  int32_t hist_len = 0;
+  size_t smem(bool with_hist, const mg_graph g) const {
+    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
+                           (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
+  }
+};
+
+Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32_t* hist_out,
+                 size_t stage_limit, int32_t split_batch) {
+  const mg_graph g = p->g;
+  Plan pl;
+  pl.f64 = p->prec == MG_FP64;
+  mg::SimArgs& a = pl.a;
   a.g = g->view;
   a.s = p->sv;
   a.c = p->cv;
   a.n = p->n;
   a.pid_base = p->pid_base;
   a.instance = p->instance;
-  const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
-  for (uint32_t r = 0; r < 10; ++r) {
-    a.rk[2 * r] = k0 + r * 0x9E3779B9u;
-    a.rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
-  }
   a.dt = dt;
   a.sqrt_dt = std::sqrt(dt);
   a.M = M;
-  a.split_batch = p->split_batch > 0 ? p->split_batch : default_split_batch(p->prec);
-  // shared-memory plan: the normal ring always; then the tables, the
-  // counters and the histogram, as long as the total stays in the budget
-  const bool want_hist = hist_bins > 0;
-  const int32_t hist_len = want_hist ? g->E * hist_bins : 0;
-  bool stage = true, counters = true, shist = want_hist;
-  auto lay = [&](bool with_hist) {
-    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
-                           (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
-  };
+  a.split_batch = split_batch > 0 ? split_batch : default_split_batch(p->prec);
+  a.hist_bins = hist_bins;
+  a.hist = hist_out;
+  pl.hist_len = hist_bins > 0 ? g->E * hist_bins : 0;
+  pl.shist = hist_bins > 0;
   const size_t budget = kSmemBudget + 128u * mg::kBlock;  // + the normal ring
-  if (lay(true) > budget) shist = false;
-  if (lay(true) > budget) counters = false;
-  if (lay(true) > budget) stage = false;
-  a.stage_smem = stage;
-  a.smem_counters = counters;
-  // launches: at most 2^31 - 1 steps (the per-lane step counter), and with
-  // 32-bit shared counters at most 2^32 / (256 (2M + 1)) so they cannot wrap
-  // (and the kernel's loop guard, 32 steps (2M + 2) + 64, fits 32 bits)
+  const size_t tables = mg::smem_layout(g->V, g->E, g->S, pl.f64, true, false, 0, mg::kBlock).total -
+                        mg::smem_layout(g->V, g->E, g->S, pl.f64, false, false, 0, mg::kBlock).total;
+  if (tables > stage_limit) pl.stage = false;
+  if (pl.smem(true, g) > budget) pl.shist = false;
+  if (pl.smem(true, g) > budget) pl.counters = false;
+  if (pl.smem(true, g) > budget) pl.stage = false;
+  a.stage_smem = pl.stage;
+  a.smem_counters = pl.counters;
+  a.smem_hist = pl.shist;
+  return pl;
+}
+
+// Most EM-Steps one launch may take: 2^31 - 1 (the per-lane step counter);
+// with 32-bit shared counters 2^32 / (256 (2M + 1)) so they cannot wrap; and
+// the kernel's loop guard, 32 steps (2M + 2) + 64, must fit 32 bits.
+int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
   int64_t chunk = (int64_t)((4294967295ull - 64ull) / (32ull * (2ull * (uint64_t)M + 2ull)));
-  if (counters) {
+  if (smem_counters) {
     const int64_t cap = (int64_t)(4294967295ull / (256ull * (2ull * (uint64_t)M + 1ull)));
     if (chunk > cap) chunk = cap;
   }
+  return chunk < 1 ? 1 : chunk;
+}
+
+mg_status check_step_args(double dt, int64_t steps, int32_t M, int32_t hist_bins,
+                          const uint32_t* hist_out) {
+  if (!(std::isfinite(dt) && dt > 0.0)) return fail(MG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (steps < 0) return fail(MG_ERR_INVALID_ARG, "steps must be >= 0");
+  if (M < 1 || M > 1024) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be in [1, 1024]");
+  if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");
+  if (hist_bins > 0 && !hist_out) return fail(MG_ERR_INVALID_ARG, "hist_bins > 0 needs hist_out");
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t M,
+                                 int32_t hist_bins, uint32_t* hist_out, void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_simulate: NULL particles");
+  mg_status s = check_step_args(dt, steps, M, hist_bins, hist_out);
+  if (s != MG_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mg_graph g = p->g;
+  Plan pl = plan_launch(p, dt, M, hist_bins, hist_out, (size_t)-1, p->split_batch);
+  const mg::Keys keys = keys_of(p->seed);
+  int64_t chunk = max_steps_per_launch(M, pl.counters);
   if (p->steps_per_launch > 0 && p->steps_per_launch < chunk) chunk = p->steps_per_launch;
-  if (chunk < 1) chunk = 1;
   int64_t done = 0;
   do {
     const int64_t now = (steps - done < chunk) ? steps - done : chunk;
-    a.steps = now;
+    pl.a.steps = now;
     const bool last = done + now >= steps;
-    a.hist_bins = (last && want_hist) ? hist_bins : 0;
-    a.hist = hist_out;
-    a.smem_hist = (last && shist) ? 1 : 0;
-    const size_t sm = lay(last);
-    cudaError_t ce;
-    switch (p->prec) {
-      case MG_FP64: ce = mg::launch_em_step_f64(a, sm, st); break;
-      case MG_FP32_MIXED: ce = mg::launch_em_step_mixed(a, sm, st); break;
-      default: ce = mg::launch_em_step_f32(a, sm, st); break;
-    }
+    pl.a.hist_bins = (last && hist_bins > 0) ? hist_bins : 0;
+    pl.a.smem_hist = (last && pl.shist) ? 1 : 0;
+    cudaError_t ce = mg::launch_em_step((int)p->prec, pl.a, keys, pl.smem(last, g), st);
     if (ce != cudaSuccess) return cuda_fail(ce, "mg_simulate: launch");
     done += now;
   } while (done < steps);
   p->step += (uint64_t)steps;
   p->last_stream = st;
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+struct mg_batch_s {
+  struct Member {
+    mg_particles p;
+    double dt;
+    int64_t steps;
+    int32_t M, hist_bins;
+    uint32_t* hist;
+  };
+  std::vector<Member> members;
+  bool have_seed = false;
+  uint64_t seed = 0;
+  mg_precision prec = MG_FP64;
+  int32_t split_batch = 0;      // 0: the precision's default
+  int64_t stage_limit = -1;     // < 0: stage whatever fits the budget
+  int32_t blocks_per_sm = 0;    // 0: occupancy maximum
+  bool dirty = true;
+  // device side (rebuilt when dirty)
+  DevBuf buf;                   // SimArgs[n_inst] | BatchItem[n_items] | head
+  mg::SimArgs* d_insts = nullptr;
+  mg::BatchItem* d_items = nullptr;
+  uint32_t* d_head = nullptr;
+  int32_t n_items = 0;
+  size_t smem = 0;
+  int blocks = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void batch_drop_graph(mg_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Builds the instance table and the work queue: one item per 256 particles,
+// instances with more steps first (longest-processing-time order).
+mg_status batch_build(mg_batch b, cudaStream_t st) {
+  const size_t n_inst = b->members.size();
+  std::vector<mg::SimArgs> insts(n_inst);
+  std::vector<size_t> order(n_inst);
+  size_t smem = 0;
+  const size_t stage_limit = b->stage_limit < 0 ? (size_t)-1 : (size_t)b->stage_limit;
+  for (size_t m = 0; m < n_inst; ++m) {
+    const auto& mb = b->members[m];
+    Plan pl = plan_launch(mb.p, mb.dt, mb.M, mb.hist_bins, mb.hist, stage_limit, b->split_batch);
+    pl.a.steps = mb.steps;
+    insts[m] = pl.a;
+    smem = std::max(smem, pl.smem(true, mb.p->g));
+    if (mb.steps > max_steps_per_launch(mb.M, pl.counters))
+      return fail(MG_ERR_INVALID_ARG, "mg_batch: member %zu takes more steps than one launch allows",
+                  m);
+    order[m] = m;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    return b->members[x].steps > b->members[y].steps;
+  });
+  std::vector<mg::BatchItem> items;
+  for (size_t m : order) {
+    if (b->members[m].steps == 0) continue;
+    const int64_t tiles = (b->members[m].p->n + mg::kBlock - 1) / mg::kBlock;
+    for (int64_t t = 0; t < tiles; ++t) items.push_back({(int32_t)m, (int32_t)t});
+  }
+  if (items.size() > 2147483647u) return fail(MG_ERR_INVALID_ARG, "mg_batch: too many work items");
+  const size_t o_inst = 0, o_items = a256(n_inst * sizeof(mg::SimArgs));
+  const size_t o_head = a256(o_items + items.size() * sizeof(mg::BatchItem));
+  const size_t total = o_head + 256;
+  if (b->buf.bytes < total) {
+    dev_free(b->buf, st);
+    mg_status s = dev_alloc(b->buf, total, st);
+    if (s != MG_OK) return s;
+  }
+  unsigned char* base = static_cast<unsigned char*>(b->buf.p);
+  b->d_insts = reinterpret_cast<mg::SimArgs*>(base + o_inst);
+  b->d_items = reinterpret_cast<mg::BatchItem*>(base + o_items);
+  b->d_head = reinterpret_cast<uint32_t*>(base + o_head);
+  MG_CUDA(cudaMemcpyAsync(b->d_insts, insts.data(), n_inst * sizeof(mg::SimArgs),
+                          cudaMemcpyHostToDevice, st));
+  if (!items.empty())
+    MG_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(mg::BatchItem),
+                            cudaMemcpyHostToDevice, st));
+  MG_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  b->n_items = (int32_t)items.size();
+  b->smem = smem;
+  int per_sm = mg::em_batch_blocks_per_sm((int)b->prec, smem);
+  if (per_sm < 1) return fail(MG_ERR_INVALID_ARG, "mg_batch: the kernel does not fit an SM");
+  if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
+  int dev = 0, sms = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  b->blocks = std::max(1, std::min(per_sm * sms, b->n_items));
+  b->dirty = false;
+  return MG_OK;
+}
+
+mg_status batch_enqueue(mg_batch b, cudaStream_t st) {
+  MG_CUDA(cudaMemsetAsync(b->d_head, 0, 4, st));
+  if (b->n_items > 0) {
+    cudaError_t ce = mg::launch_em_batch((int)b->prec, b->d_insts, b->d_items, b->n_items, b->d_head,
+                                         keys_of(b->seed), b->smem, b->blocks, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "mg_batch_run: launch");
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_batch_create(mg_batch* out) {
+  if (!out) return fail(MG_ERR_INVALID_ARG, "mg_batch_create: NULL argument");
+  *out = new mg_batch_s();
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_add(mg_batch b, mg_particles p, double dt, int64_t steps, int32_t M,
+                                  int32_t hist_bins, uint32_t* hist_out) {
+  if (!b || !p) return fail(MG_ERR_INVALID_ARG, "mg_batch_add: NULL argument");
+  mg_status s = check_step_args(dt, steps, M, hist_bins, hist_out);
+  if (s != MG_OK) return s;
+  if (b->members.empty()) {
+    b->seed = p->seed;
+    b->prec = p->prec;
+  } else {
+    if (p->seed != b->seed) return fail(MG_ERR_INVALID_ARG, "mg_batch_add: members share one seed");
+    if (p->prec != b->prec) return fail(MG_ERR_INVALID_ARG, "mg_batch_add: members share one precision");
+  }
+  for (const auto& m : b->members)
+    if (m.p == p) return fail(MG_ERR_INVALID_ARG, "mg_batch_add: a particle set is already a member");
+  b->members.push_back({p, dt, steps, M, hist_bins, hist_out});
+  b->dirty = true;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_clear(mg_batch b) {
+  if (!b) return fail(MG_ERR_INVALID_ARG, "mg_batch_clear: NULL batch");
+  b->members.clear();
+  b->dirty = true;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_set_tuning(mg_batch b, int32_t split_batch, int64_t stage_limit_bytes,
+                                         int32_t blocks_per_sm) {
+  if (!b) return fail(MG_ERR_INVALID_ARG, "mg_batch_set_tuning: NULL batch");
+  if (split_batch < 0 || split_batch > 32 || blocks_per_sm < 0)
+    return fail(MG_ERR_INVALID_ARG, "mg_batch_set_tuning: split_batch in [0, 32], blocks_per_sm >= 0");
+  b->split_batch = split_batch;
+  b->stage_limit = stage_limit_bytes;
+  b->blocks_per_sm = blocks_per_sm;
+  b->dirty = true;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_run(mg_batch b, int use_graph, void* stream) {
+  if (!b) return fail(MG_ERR_INVALID_ARG, "mg_batch_run: NULL batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (use_graph && st == nullptr)
+    return fail(MG_ERR_INVALID_ARG, "mg_batch_run: graph replay needs a non-default stream");
+  if (b->dirty) {
+    batch_drop_graph(b);
+    mg_status s = batch_build(b, st);
+    if (s != MG_OK) return s;
+  }
+  if (use_graph) {
+    if (!b->exec || b->graph_stream != st) {
+      batch_drop_graph(b);
+      MG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      mg_status s = batch_enqueue(b, st);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (s != MG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "mg_batch_run: capture");
+      b->graph = graph;
+      MG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+      b->graph_stream = st;
+    }
+    MG_CUDA(cudaGraphLaunch(b->exec, st));
+  } else {
+    mg_status s = batch_enqueue(b, st);
+    if (s != MG_OK) return s;
+  }
+  for (auto& m : b->members) {
+    m.p->step += (uint64_t)m.steps;
+    m.p->last_stream = st;
+  }
+  b->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_info(mg_batch b, int32_t* n_members, int32_t* n_items,
+                                   int32_t* blocks) {
+  if (!b) return fail(MG_ERR_INVALID_ARG, "mg_batch_info: NULL batch");
+  if (n_members) *n_members = (int32_t)b->members.size();
+  if (n_items) *n_items = b->n_items;
+  if (blocks) *blocks = b->blocks;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_batch_destroy(mg_batch b) {
+  if (!b) return MG_OK;
+  cudaStreamSynchronize(b->last_stream);
+  batch_drop_graph(b);
+  dev_free(b->buf, b->last_stream);
+  delete b;
   return MG_OK;
 }
 

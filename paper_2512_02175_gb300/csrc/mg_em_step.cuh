@@ -298,7 +298,7 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
 // that would pass 2^32 - 16 normals stops with kErrStream.
 template <int kMode>
 __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R* ring,
-                                       const SimArgs& a, uint32_t pid) {
+                                       const SimArgs& a, const Keys& keys, uint32_t pid) {
   using R = typename Types<kMode>::R;
   if (p.n_gen >= 0xFFFFFFF0u) {
     atomicOr(a.c.err, kErrStream);
@@ -306,7 +306,7 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
     p.pending = false;
     return;
   }
-  const U4 w = philox4x32_10(p.n_gen >> 2, pid, 0u, a.instance, a.rk);
+  const U4 w = philox4x32_10(p.n_gen >> 2, pid, 0u, a.instance, keys.rk);
   R z0, z1, z2, z3;
   if constexpr (kMode == kModeF64) {
     box_muller_f64(w.x, w.y, z0, z1);
@@ -417,8 +417,9 @@ __device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Typ
 // jump draw, next edge, and the coefficients of the rest of the step.
 template <int kMode>
 __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
-                                      const BlockCounters& bc, const typename Types<kMode>::R* ring,
-                                      uint32_t pid, uint32_t& trunc) {
+                                      const Keys& keys, const BlockCounters& bc,
+                                      const typename Types<kMode>::R* ring, uint32_t pid,
+                                      uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   using H = typename Types<kMode>::H;
   p.pending = false;
@@ -471,7 +472,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.active = false;
     return;
   }
-  const U4 w = philox4x32_10(j, pid, 1u, a.instance, a.rk);
+  const U4 w = philox4x32_10(j, pid, 1u, a.instance, keys.rk);
   const int32_t slot = choose_slot(g, vr, w.x);
   const SlotRec sr = g.slot[slot];
   enter_edge<kMode>(p, g, sr.edge, a);
@@ -522,10 +523,12 @@ __device__ __forceinline__ void block_zero(T* dst, int32_t n) {
 
 // ------------------------------------------------------------- the kernel
 
+// One block's tile of a particle set: particle i of the calling thread
+// (i >= a.n: an idle lane that still takes part in the block's barriers).
 template <int kMode>
-__global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ SimArgs a) {
+__device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int64_t i,
+                                         unsigned char* smem) {
   using R = typename Types<kMode>::R;
-  extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool kF64 = kMode == kModeF64;
   GraphView g = a.g;
   const int32_t hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
@@ -558,7 +561,6 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
 
   uint32_t trunc = 0;
   uint64_t psteps = 0;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t pid = a.pid_base + (uint32_t)i;
   Lane<kMode> p;
   p.active = false;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
         set_vertex_sign(p, end);
       }
       p.n_gen = p.n_draw & ~3u;
-      refill<kMode>(p, ring, a, pid);
+      refill<kMode>(p, ring, a, keys, pid);
     }
   }
 
@@ -623,14 +625,15 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
     }
     const uint32_t pm = __ballot_sync(full, p.pending);
     if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
-      if (p.pending) split<kMode>(p, g, a, bc, ring, pid, trunc);
+      if (p.pending) split<kMode>(p, g, a, keys, bc, ring, pid, trunc);
     }
     // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
     // lane that went pending with an empty buffer needs up to three refills)
     constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
 #pragma unroll
     for (int f = 0; f < (int)(kSub + 4) / 4; ++f)
-      if (p.active && !p.pending && p.n_gen - p.n_draw <= kSub) refill<kMode>(p, ring, a, pid);
+      if (p.active && !p.pending && p.n_gen - p.n_draw <= kSub)
+        refill<kMode>(p, ring, a, keys, pid);
     if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
     const bool run = p.active && !p.pending && !p.at_v;
     if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
@@ -677,6 +680,42 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
   if (shist)
     for (int32_t k = threadIdx.x; k < hist_len; k += blockDim.x)
       if (shist[k]) atomicAdd(&a.hist[k], shist[k]);
+}
+
+// The fused EM-Step kernel over one particle set: block b takes particles
+// b * 256 .. b * 256 + 255.
+template <int kMode>
+__global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ SimArgs a,
+                                                      const __grid_constant__ Keys keys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  run_tile<kMode>(a, keys, (int64_t)blockIdx.x * kThreads + threadIdx.x, smem);
+}
+
+// The batched, persistent form: each block pops work items -- 256 particles
+// of one instance -- from a queue (ordered longest first by the host) until
+// it is empty, copying the instance's arguments to shared memory and running
+// the same tile body, so a particle's result does not depend on the batch.
+template <int kMode>
+__global__ void __launch_bounds__(256) em_batch_kernel(const SimArgs* __restrict__ insts,
+                                                       const BatchItem* __restrict__ items,
+                                                       int32_t n_items, uint32_t* head,
+                                                       const __grid_constant__ Keys keys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) SimArgs sa;
+  __shared__ int32_t s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int32_t)atomicAdd(head, 1u);
+    __syncthreads();
+    const int32_t it = s_item;
+    if (it >= n_items) break;
+    const BatchItem bi = items[it];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(insts + bi.inst);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+    for (int k = threadIdx.x; k < (int)(sizeof(SimArgs) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    run_tile<kMode>(sa, keys, (int64_t)bi.tile * kThreads + threadIdx.x, smem);
+    __syncthreads();
+  }
 }
 
 // Snapshot histogram of the living particles (no stepping).

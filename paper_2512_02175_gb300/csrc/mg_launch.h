@@ -8,11 +8,29 @@ namespace mg {
 
 constexpr int kBlock = kThreads;
 
-// Fused EM-Step kernel: binary64 (em_step_f64.cu), binary32-mixed and
-// binary32 (em_step_f32.cu).
-cudaError_t launch_em_step_f64(const SimArgs& a, size_t smem, cudaStream_t st);
-cudaError_t launch_em_step_mixed(const SimArgs& a, size_t smem, cudaStream_t st);
-cudaError_t launch_em_step_f32(const SimArgs& a, size_t smem, cudaStream_t st);
+// Fused EM-Step kernel over one particle set, by precision mode (kModeF64 in
+// em_step_f64.cu, kModeMixed and kModeF32 in em_step_f32.cu).
+cudaError_t launch_em_step(int mode, const SimArgs& a, const Keys& k, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cudaStream_t st);
+cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
+                                cudaStream_t st);
+
+// The batched persistent kernel: `blocks` blocks pop the n_items work items
+// (head must be zero at launch).  blocks_per_sm: resident blocks per SM at
+// `smem` bytes of dynamic shared memory.
+cudaError_t launch_em_batch(int mode, const SimArgs* insts, const BatchItem* items, int32_t n_items,
+                            uint32_t* head, const Keys& k, size_t smem, int blocks,
+                            cudaStream_t st);
+cudaError_t launch_em_batch_f64(const SimArgs* insts, const BatchItem* items, int32_t n_items,
+                                uint32_t* head, const Keys& k, size_t smem, int blocks,
+                                cudaStream_t st);
+cudaError_t launch_em_batch_f32x(int mode, const SimArgs* insts, const BatchItem* items,
+                                 int32_t n_items, uint32_t* head, const Keys& k, size_t smem,
+                                 int blocks, cudaStream_t st);
+int em_batch_blocks_per_sm(int mode, size_t smem);
+int em_batch_blocks_per_sm_f64(size_t smem);
+int em_batch_blocks_per_sm_f32x(int mode, size_t smem);
 
 // Snapshot histogram of the living particles (adds into out); x is binary32
 // or binary64.

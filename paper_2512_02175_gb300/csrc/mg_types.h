@@ -74,7 +74,13 @@ struct CounterView {
   uint32_t* err;                 // [1] device-error bits
 };
 
-// Everything one launch of the fused EM-Step kernel needs.
+// Philox round keys of a seed: (seed lo + r W0, seed hi + r W1), r = 0..9.
+struct Keys {
+  uint32_t rk[20];
+};
+
+// One particle set's share of a launch of the fused EM-Step kernel (the
+// whole launch for mg_simulate, one instance of a batch otherwise).
 struct SimArgs {
   GraphView g;
   StateView s;
@@ -82,8 +88,6 @@ struct SimArgs {
   int64_t n;
   uint32_t pid_base;
   uint32_t instance;
-  uint32_t rk[20];      // Philox round keys: (seed lo + r W0, seed hi + r W1), r = 0..9
-  uint64_t t_begin;     // global index of the first step of this launch
   int64_t steps;
   double dt, sqrt_dt;
   int32_t M;
@@ -124,5 +128,12 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
   l.total = off;
   return l;
 }
+
+// A work item of the batched kernel: 256 particles (one block) of an
+// instance, from particle tile * kThreads on.
+struct BatchItem {
+  int32_t inst;
+  int32_t tile;
+};
 
 }  // namespace mg

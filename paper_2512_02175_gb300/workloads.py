@@ -306,6 +306,38 @@ def inject_at_inlets(d, n: int, seed: int):
     return edge, x.astype(np.float64)
 
 
+def star_quadratic(k: int, seed: int):
+    """Star of k edges, lognormal lengths (median 1, sigma_log 0.5), quadratic
+    potentials as in ``star_langevin``, sigma = sqrt(2), equal b."""
+    r = _rng(seed)
+    L = np.exp(r.normal(0.0, 0.5, k))
+    a = r.uniform(0.5, 4.0, k)
+    c = r.uniform(0.0, 1.0, k) * L
+    return _desc(k + 1, np.zeros(k, np.int32), np.arange(1, k + 1), L, 2.0 * a * c, -2.0 * a,
+                 math.sqrt(2.0), 1.0, 1.0)
+
+
+def batch_instances(n_inst: int = 512, seed: int = 4, n_scale: float = 1.0,
+                    steps_scale: float = 1.0, max_tree_edges: int = 10_000):
+    """Uneven instances for one batched launch: half stars with K ~ U{3..64}
+    edges, half uniform random trees with E ~ log-U[100, max_tree_edges]; each
+    with N ~ 2^U[12, 22] particles (times n_scale), steps ~ U{100..5000}
+    (times steps_scale), dt = 1e-3, M = 16.  Returns a list of dicts with the
+    graph description, n, steps, dt, M and a graph seed."""
+    r = _rng(seed)
+    out = []
+    for i in range(n_inst):
+        if i % 2 == 0:
+            g = star_quadratic(int(r.integers(3, 65)), seed=1000 + i)
+        else:
+            E = int(round(math.exp(r.uniform(math.log(100), math.log(max_tree_edges)))))
+            g = random_tree(E, seed=1000 + i)
+        n = max(32, int(round(2.0 ** r.uniform(12, 22) * n_scale)))
+        steps = max(1, int(round(r.integers(100, 5001) * steps_scale)))
+        out.append(dict(graph=g, n=n, steps=steps, dt=1e-3, M=16, instance=i))
+    return out
+
+
 CONFIGS = {
     "star3_brownian": dict(graph=lambda: star_brownian(3), n=10_000, dt=1e-3, steps=1000, M=8,
                            bins=32, seed=0, init="round_robin"),
