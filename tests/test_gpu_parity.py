@@ -372,3 +372,33 @@ def test_star16_coupled_tv_fp32_vs_fp64_full_n(B):
     g.close()
     tv = 0.5 * np.abs(hs[0] - hs[1]).sum() / n
     assert tv <= 1e-3, tv
+
+
+# ------------------------------------------------ synthetic vascular graph
+
+def test_vascular_fp64_trajectories(B):
+    """The vascular stand-in (5000 points): drift-dominated edges, many
+    splits per step, absorbing outlets, tracer injected at the inlets."""
+    d = W.vascular(n_points=5000)
+    n = 4096
+    e, x = W.inject_at_inlets(d, n, 3)
+    gs, gc, gh = gpu_run(B, d, e, x, seed=2, dt=d["dt"], steps=300, M=32, prec=B.MG_FP64, bins=4)
+    o = oracle_pool.run(d, e, x, seed=2, dt=d["dt"], steps=300, M=32, bins=4)
+    assert_fp64_parity(gs, gc, o, ghist=gh)
+    assert gc["absorbed"].sum() > 0
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_vascular_fp32_statistics(B, prec):
+    d = W.vascular(n_points=5000)
+    n = 1 << 15
+    e, x = W.inject_at_inlets(d, n, 5)
+    gs, gc, _ = gpu_run(B, d, e, x, seed=4, dt=d["dt"], steps=400, M=32, prec=MODES[prec])
+    o = oracle_pool.run(d, e, x, seed=4, dt=d["dt"], steps=400, M=32)
+    # absorbed fraction and the coupled per-particle fate
+    fa_g, fa_o = (gs["edge"] < 0).mean(), (o["edge"] < 0).mean()
+    assert abs(fa_g - fa_o) <= 3 * np.sqrt(fa_o * (1 - fa_o) / n) + 1e-9
+    assert (gs["edge"] == o["edge"]).mean() > 0.8
+    ao, ag = o["absorbed"].astype(float), gc["absorbed"].astype(float)
+    top = np.argsort(-ao)[:10]  # the busiest outlets
+    assert np.all(np.abs(ag[top] - ao[top]) <= 4 * np.sqrt(ao[top]) + 3)

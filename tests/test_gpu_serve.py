@@ -1,0 +1,60 @@
+"""The served request loop on the GPU: a Poisson stream of requests of
+different graphs, sizes, horizons and dt, admitted under a memory budget,
+advanced in continuous-batching rounds on two streams.  Each request's final
+state, counters and histogram are bit-identical to running it alone."""
+import numpy as np
+import pytest
+
+from paper_2512_02175_gb300 import serve
+from paper_2512_02175_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    return {"star3": W.star_brownian(3), "star16": W.star_langevin(16),
+            "vascular": W.vascular(n_points=3000)}
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_served_equals_alone(prec):
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    graphs = _graphs()
+    reqs = serve.poisson_trace(400.0, 0.08, 3, graphs, n_range=(9, 13), steps_range=(20, 400),
+                               init=serve.default_init)
+    assert len(reqs) >= 12
+    be = serve.GpuBackend(graphs, prec, seed=7, n_lanes=2)
+    total = sum(be.bytes_of(r) for r in reqs)
+    srv = serve.Server(be, mem_budget=max(total // 3, max(be.bytes_of(r) for r in reqs)),
+                       n_lanes=2, chunk_steps=64, keep_state=True)
+    res = srv.run_trace(reqs, time_limit=300)
+    assert sorted(r.rid for r in res) == [q.rid for q in sorted(reqs, key=lambda q: q.rid)]
+    assert srv.peak_reserved <= srv.mem_budget
+    by = {r.rid: r for r in res}
+    G = {k: B.Graph(d) for k, d in graphs.items()}
+    for q in reqs:
+        p = B.Particles(G[q.graph], q.edge0, q.x0, seed=7, instance=q.rid, precision=prec)
+        p.simulate(q.dt, q.steps, q.M)
+        st, cn, h = p.state(), p.counts(), p.histogram(q.bins)
+        p.close()
+        r = by[q.rid]
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+            assert np.array_equal(st[k], r.state[k]), (q.rid, k)
+        assert np.array_equal(cn["exits"], r.counts["exits"])
+        assert np.array_equal(cn["absorbed"], r.counts["absorbed"])
+        assert cn["truncations"] == r.counts["truncations"]
+        assert np.array_equal(h, r.hist)
+    s = serve.latency_summary(res)
+    assert s["p99_s"] >= s["p50_s"] > 0
+    be.close()
+
+
+def test_plain_path_runs():
+    graphs = _graphs()
+    reqs = serve.poisson_trace(200.0, 0.03, 5, graphs, n_range=(8, 10), steps_range=(10, 50),
+                               init=serve.default_init)
+    res = serve.serve_plain(reqs, graphs, 0, seed=7)
+    assert len(res) == len(reqs)
+    assert all(r.particle_steps > 0 for r in res)

@@ -1,0 +1,136 @@
+"""Admission and scheduling of the served request loop, on the CPU with a
+fake backend (no GPU): memory budget respected, FIFO admission, continuous
+batching in rounds of at most chunk_steps, several lanes in flight, every
+request completed exactly once with all its steps."""
+import numpy as np
+import pytest
+
+from paper_2512_02175_gb300 import serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeBackend:
+    """Rounds complete after a fixed number of polls; records every launch."""
+
+    def __init__(self, delay_polls=2):
+        self.delay = delay_polls
+        self.launches = []
+        self.live = {}
+        self.steps_done = {}
+
+    def bytes_of(self, req):
+        return req.n * 24
+
+    def admit(self, req):
+        self.live[req.rid] = req
+        self.steps_done[req.rid] = 0
+        return req.rid
+
+    def launch(self, lane, members):
+        for rid, s in members:
+            assert rid in self.live
+            self.steps_done[rid] += s
+        tok = {"polls": 0, "lane": lane, "members": list(members)}
+        self.launches.append(tok)
+        return tok
+
+    def poll(self, tok):
+        tok["polls"] += 1
+        return tok["polls"] > self.delay
+
+    def collect(self, rid, keep_state):
+        req = self.live[rid]
+        return np.zeros(4, np.uint32), {"particle_steps": req.n * req.steps}, None
+
+    def release(self, rid):
+        del self.live[rid]
+
+
+def _reqs(k, seed=0):
+    r = np.random.default_rng(seed)
+    return [serve.Request(i, "g", int(r.integers(100, 2000)), int(r.integers(1, 3000)), 1e-3)
+            for i in range(k)]
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_all_requests_complete_within_budget(lanes):
+    be = FakeBackend()
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=60_000, n_lanes=lanes, chunk_steps=500, clock=clk)
+    reqs = _reqs(40)
+    for q in reqs:
+        srv.submit(q)
+    for _ in range(100_000):
+        if srv.idle():
+            break
+        srv.step()
+        clk.t += 1.0
+        assert srv.reserved <= 60_000
+        assert sum(1 for l in srv.lanes if l is not None) <= lanes
+    assert srv.idle()
+    assert sorted(r.rid for r in srv.results) == list(range(40))
+    for q in reqs:
+        assert be.steps_done[q.rid] == q.steps
+    assert srv.peak_reserved <= 60_000
+    # no round gives a request more than chunk_steps, and a request is never
+    # in two rounds at once
+    for tok in be.launches:
+        assert all(s <= 500 for _, s in tok["members"])
+    assert not be.live
+
+
+def test_fifo_admission_blocks_behind_large_request():
+    be = FakeBackend()
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=10_000, n_lanes=2, chunk_steps=100, clock=clk)
+    big = serve.Request(0, "g", 400, 300, 1e-3)      # 9600 bytes
+    small = serve.Request(1, "g", 10, 10, 1e-3)      # 240 bytes: would fit, but waits its turn
+    big2 = serve.Request(2, "g", 300, 10, 1e-3)
+    for q in (big, big2, small):
+        srv.submit(q)
+    srv.step()
+    assert [a.req.rid for a in srv.active] == [0]
+    assert [q.rid for q in srv.queue] == [2, 1]
+
+
+def test_request_larger_than_budget_rejected():
+    srv = serve.Server(FakeBackend(), mem_budget=100, clock=FakeClock())
+    with pytest.raises(ValueError):
+        srv.submit(serve.Request(0, "g", 1000, 10, 1e-3))
+
+
+def test_new_arrivals_join_next_round():
+    be = FakeBackend(delay_polls=0)
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=10**9, n_lanes=1, chunk_steps=100, clock=clk)
+    srv.submit(serve.Request(0, "g", 10, 1000, 1e-3))
+    srv.step()  # round 1: request 0 alone
+    srv.submit(serve.Request(1, "g", 10, 1000, 1e-3))
+    for _ in range(3):
+        srv.step()
+    members = [[rid for rid, _ in t["members"]] for t in be.launches]
+    assert members[0] == [0]
+    assert any(m == [0, 1] for m in members[1:])
+
+
+def test_latency_summary():
+    res = [serve.Result(i, np.zeros(1), {}, None, 0.0, 0.0, float(i + 1), 100) for i in range(100)]
+    s = serve.latency_summary(res, 0.0, 100.0)
+    assert s["requests"] == 100 and abs(s["p50_s"] - 50.5) < 1e-9 and s["p99_s"] > 98.9
+    assert s["served_particle_steps_per_s"] == 100.0
+
+
+def test_poisson_trace_shape():
+    tr = serve.poisson_trace(200.0, 5.0, 1, {"a": None, "b": None})
+    assert 800 < len(tr) < 1200
+    arr = np.array([q.arrival for q in tr])
+    assert np.all(np.diff(arr) > 0) and arr[-1] <= 5.0
+    assert all(2 ** 14 - 1 <= q.n <= 2 ** 24 + 1 for q in tr)
+    assert all(100 <= q.steps <= 5000 for q in tr)
