@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16_384)
+    ap.add_argument("--workload", default="star16_langevin",
+                    choices=["star16_langevin", "vascular", "batch512", "served"],
+                    help="star16_langevin is the headline; the others report the "
+                         "vascular, batched and served configurations")
     return ap.parse_args()
 
 
@@ -331,10 +335,195 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------- other configurations
+
+def _mode(B, precision):
+    return {"mixed": B.MG_FP32_MIXED, "fp32": B.MG_FP32, "fp64": B.MG_FP64}[precision]
+
+
+def _events(torch, k):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+
+
+def run_vascular(args):
+    """The synthetic vascular network: 2^26 tracers injected at the inlets,
+    2000 EM-Steps (dt = 10x the explicit one-cell finite-volume limit), M = 32,
+    16-bin histograms; each benchmark step restarts from the injected state
+    (device-resident) so every step does the same work."""
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    d = W.vascular()
+    n = 1 << 26 if args.n == (1 << 24) else args.n
+    steps, Mv, bins = 2000, 32, 16
+    e0, x0 = W.inject_at_inlets(d, n, 11)
+    B.load()
+    B.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    g = B.Graph(d)
+    de, dx = torch.from_numpy(e0).cuda(), torch.from_numpy(x0).cuda()
+    p = B.Particles(g, de, dx, seed=SEED, precision=_mode(B, args.precision), stream=stream)
+    hist = torch.zeros(g.n_edges * bins, dtype=torch.int32, device="cuda")
+
+    def step():
+        p.reset(de, dx, stream)
+        hist.zero_()
+        p.simulate(d["dt"], steps, Mv, bins, hist, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    ev = _events(torch, args.steps)
+    ps = 0
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    c = p.counts(stream)
+    ps = c["particle_steps"] * args.steps  # counters restart with every reset
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    out = {"metric": METRIC, "value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "data": "synthetic",
+           "config": {"workload": "vascular", "vertices": int(d["n_vertices"]),
+                      "edges": int(len(d["src"])), "n_particles": n, "dt_s": d["dt"],
+                      "em_steps_per_step": steps, "M": Mv, "hist_bins_per_edge": bins,
+                      "precision": args.precision},
+           "absorbed_fraction": float(sum(c["absorbed"]) / n),
+           "truncations_per_step": c["truncations"] / steps, "launch_ms": ms}
+    p.close()
+    g.close()
+    print(json.dumps(out))
+    return 0
+
+
+def run_batch512(args):
+    """512 uneven instances (stars with 3..64 edges, random trees with
+    100..10^4 edges, N ~ 2^U[12,22], 100..5000 steps) in one persistent launch,
+    replayed from a captured CUDA graph, with autotuned launch tuning."""
+    import torch
+    from paper_2512_02175_gb300 import autotune as A
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    B.use_torch_allocator()
+    insts = W.batch_instances(512)
+    prec = _mode(B, args.precision)
+    graphs, parts = [], []
+    for k, it in enumerate(insts):
+        g = B.Graph(it["graph"])
+        e, x = W.uniform_on_edges(it["graph"], it["n"], 100 + k)
+        parts.append(B.Particles(g, e, x, seed=SEED, instance=k, precision=prec))
+        graphs.append(g)
+    stream = torch.cuda.Stream()
+
+    def make(steps_of):
+        b = B.Batch()
+        for p, it in zip(parts, insts):
+            b.add(p, it["dt"], steps_of(it), it["M"])
+        return b
+
+    def trial(t):
+        b = make(lambda it: max(1, it["steps"] // 50))
+        b.set_tuning(**t.as_dict())
+        b.run(False, stream)  # build
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run(False, stream)
+        torch.cuda.synchronize()
+        dt_ = time.perf_counter() - t0
+        b.close()
+        return dt_
+
+    key = f"{torch.cuda.get_device_name()}-prec{prec}-batch512"
+    tun = A.tune(key, trial)
+    b = make(lambda it: it["steps"])
+    b.set_tuning(**tun.as_dict())
+    for _ in range(args.warmup):
+        b.run(True, stream)
+    torch.cuda.synchronize()
+    c0 = sum(p.counts(stream)["particle_steps"] for p in parts)
+    ev = _events(torch, args.steps)
+    ev[0].record(stream)
+    for k in range(args.steps):
+        b.run(True, stream)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ps = sum(p.counts(stream)["particle_steps"] for p in parts) - c0
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    n_members, n_items, blocks = b.info()
+    out = {"metric": METRIC, "value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "data": "synthetic",
+           "config": {"workload": "batch512", "instances": n_members, "work_items": n_items,
+                      "persistent_blocks": blocks, "particles": int(sum(i["n"] for i in insts)),
+                      "particle_steps_per_step": int(sum(i["n"] * i["steps"] for i in insts)),
+                      "cuda_graph": True, "tuning": tun.as_dict(), "precision": args.precision},
+           "launch_ms": ms}
+    b.close()
+    for p in parts:
+        p.close()
+    for g in graphs:
+        g.close()
+    print(json.dumps(out))
+    return 0
+
+
+def run_served(args):
+    """A Poisson request stream (200 requests/s over 3 s) over the 3-edge
+    Brownian star, the 16-edge Langevin star and the vascular network; n =
+    2^U[12,18], steps log-U[100, 5000], dt log-U[1e-4, 1e-2].  The continuous-
+    batching server (binary32-mixed, 2 streams, rounds of 500 steps, 32 GB
+    admission budget) against the plain path: each request alone as one FP64
+    mg_simulate, in arrival order."""
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    from paper_2512_02175_gb300 import serve
+    B.load()
+    B.use_torch_allocator()
+    graphs = {"star3": W.star_brownian(3), "star16": W.star_langevin(16),
+              "vascular": W.vascular()}
+    trace = lambda: serve.poisson_trace(200.0, 3.0, 17, graphs, n_range=(12, 18),
+                                         init=serve.default_init)
+    be = serve.GpuBackend(graphs, _mode(B, args.precision), seed=SEED, n_lanes=2)
+    srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500)
+    # warm-up: a short trace (allocator, module load, graph capture paths)
+    warm = serve.poisson_trace(200.0, 0.2, 99, graphs, n_range=(10, 12), init=serve.default_init)
+    srv.run_trace(warm)
+    srv.results = []
+    torch.cuda.synchronize()
+    res = srv.run_trace(trace())
+    served = serve.latency_summary(res)
+    be.close()
+    plain = serve.latency_summary(serve.serve_plain(trace(), graphs, B.MG_FP64, seed=SEED))
+    out = {"metric": METRIC, "value": served["served_particle_steps_per_s"],
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": "served", "rate_per_s": 200, "window_s": 3.0,
+                      "n_range_log2": [12, 18], "steps_range": [100, 5000],
+                      "dt_range": [1e-4, 1e-2], "precision": args.precision,
+                      "lanes": 2, "chunk_steps": 500},
+           "served": served, "plain_fp64_per_request": plain}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "vascular":
+        return run_vascular(args)
+    if args.workload == "batch512":
+        return run_batch512(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -625,7 +625,18 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
     }
     const uint32_t pm = __ballot_sync(full, p.pending);
     if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
-      if (p.pending) split<kMode>(p, g, a, keys, bc, ring, pid, trunc);
+      // resolve each pending lane's whole chain of vertex hits in this pass:
+      // split, then the sub-step from the vertex, which may hit again (at
+      // most M times: the M-th split ends the step)
+      while (p.pending) {
+        split<kMode>(p, g, a, keys, bc, ring, pid, trunc);
+        if (!p.active || !p.in_cont) break;
+        if (p.n_gen == p.n_draw) {  // the chain has used up the buffer
+          refill<kMode>(p, ring, a, keys, pid);
+          if (!p.active) break;
+        }
+        vertex_sub_step<kMode>(p, ring, a, bc);
+      }
     }
     // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
     // lane that went pending with an empty buffer needs up to three refills)

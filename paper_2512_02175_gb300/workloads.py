@@ -223,11 +223,10 @@ def vascular(seed: int = 3, n_points: int = 50_000, knn: int = 3, max_degree: in
     g = math.pi * rad ** 4 / (8.0 * L)
     deg = np.bincount(np.concatenate([src, dst]), minlength=V)
     bnd = deg == 1
-    inlet = bnd & (z > 0.5)
-    outlet = bnd & ~inlet
+    high = bnd & (z > 0.5)
     p_fix = np.zeros(V)
-    p_fix[inlet] = r.uniform(60.0, 80.0, inlet.sum())
-    p_fix[outlet] = r.uniform(10.0, 20.0, outlet.sum())
+    p_fix[high] = r.uniform(60.0, 80.0, high.sum())
+    p_fix[bnd & ~high] = r.uniform(10.0, 20.0, (bnd & ~high).sum())
     # Kirchhoff: sum_e g_e (p_v - p_w) = 0 at interior vertices
     Lap = sp.coo_matrix((np.concatenate([g, g, -g, -g]),
                          (np.concatenate([src, dst, src, dst]),
@@ -237,6 +236,14 @@ def vascular(seed: int = 3, n_points: int = 50_000, knn: int = 3, max_degree: in
     p = p_fix.copy()
     p[free] = spl.spsolve(Lap[free][:, free].tocsc(), rhs)
     Q = g * (p[src] - p[dst])  # positive: flow from src to dst
+    # boundary vertices by the solved flow: where it enters the network an
+    # inlet (reflecting), where it leaves an outlet (absorbing) -- a
+    # reflecting wall that the flow runs into would trap particles at it
+    net_in = np.zeros(V)
+    np.add.at(net_in, src, -Q)
+    np.add.at(net_in, dst, Q)
+    inlet = bnd & (net_in < 0)   # flow leaves the vertex into its edge
+    outlet = bnd & ~inlet
     area = math.pi * rad ** 2
     u = Q / area
     u *= u_median / np.median(np.abs(u))
