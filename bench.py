@@ -185,16 +185,22 @@ def run_reference(args):
 
 def _traffic(kernel_hash):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "em_step_star16_traffic.json")
+    on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "em_step_star16_langevin.md")
+    rec = {}
     try:
         with open(path) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and line.split(":", 1)[0] in ("kernel-sha256",
+                                                            "dram-bytes-per-launch-full-size"):
+                    k, v = line.split(":", 1)
+                    rec[k] = v.strip()
+    except OSError:
         return None
-    if rec.get("kernel_sha256") != kernel_hash:
+    if rec.get("kernel-sha256") != kernel_hash:
         return None
-    return rec.get("dram_bytes_per_launch_full_size")
+    v = rec.get("dram-bytes-per-launch-full-size")
+    return int(v) if v else None
 
 
 def kernel_hash():
