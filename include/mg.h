@@ -177,7 +177,7 @@ mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t s
  * stays at the vertex and counts a truncation; Theorem 1); an absorbing
  * vertex removes the particle.  Exits (a sub-step from a vertex that ends
  * inside its edge), absorptions and truncations accumulate into the set's
- * counters.  dt > 0 finite, steps >= 0, max_splits_M >= 1.
+ * counters.  1e-30 <= dt <= 1e30, steps >= 0, max_splits_M >= 1.
  * If hist_bins > 0 and hist_out != NULL, the snapshot occupancy histogram of
  * the final positions (as mg_histogram) is ADDED to the device array
  * hist_out[n_edges * hist_bins] (uint32, caller-zeroed) in the same kernel.

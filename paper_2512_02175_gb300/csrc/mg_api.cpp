@@ -545,6 +545,8 @@ Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32
   a.instance = p->instance;
   a.dt = dt;
   a.sqrt_dt = std::sqrt(dt);
+  a.dt_f = (float)a.dt;
+  a.sqrt_dt_f = (float)a.sqrt_dt;
   a.M = M;
   a.split_batch = split_batch > 0 ? split_batch : default_split_batch(p->prec);
   a.hist_bins = hist_bins;
@@ -578,7 +580,8 @@ int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
 
 mg_status check_step_args(double dt, int64_t steps, int32_t M, int32_t hist_bins,
                           const uint32_t* hist_out) {
-  if (!(std::isfinite(dt) && dt > 0.0)) return fail(MG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  // the binary32 modes carry dt and the time left as normal binary32 numbers
+  if (!(dt >= 1e-30 && dt <= 1e30)) return fail(MG_ERR_INVALID_ARG, "dt must be in [1e-30, 1e30]");
   if (steps < 0) return fail(MG_ERR_INVALID_ARG, "steps must be >= 0");
   if (M < 1 || M > 1024) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be in [1, 1024]");
   if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");

@@ -109,6 +109,28 @@ __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& 
   zs = -r * s;
 }
 
+// ------------------------------------------- binary32 <-> binary64 by bits
+
+// Exact widening of a binary32 s in [2^-126, 1] to binary64 with integer
+// operations (sign 0, exponent rebiased by 1023 - 127, mantissa shifted up 29
+// bits), keeping the conversion off the binary64 pipe.
+__device__ __forceinline__ double widen_unit_f32(float s) {
+  const uint32_t b = __float_as_uint(s);
+  return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+
+// binary64 h in [2^-126, 2^127] to binary32, rounded to nearest even (the
+// result of an IEEE conversion), with integer operations; values below
+// 2^-126 give 0.
+__device__ __forceinline__ float narrow_f64_rn(double h) {
+  const uint32_t hi = (uint32_t)__double2hiint(h), lo = (uint32_t)__double2loint(h);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  uint32_t f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t r = lo & 0x1fffffffu;  // the 29 bits rounded away
+  f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  return (e < 897u) ? 0.0f : __uint_as_float(f);
+}
+
 // ---------------------------------------------------- hitting-fraction root
 
 // First root s in [0, 1] of A s^2 + B s + C = 0 with C >= 0 (s = sqrt(alpha)
@@ -257,15 +279,16 @@ __device__ __forceinline__ void enter_edge(Lane<kMode>& p, const GraphView& g, i
   } else {
     const EdgeRec32& q = g.e32[e];
     p.L = q.L;
-    p.Pm = q.c0 * (float)a.dt;
-    p.Qm = fmaf(q.c1, (float)a.dt, 1.0f);
-    p.Sm = q.sigma * (float)a.sqrt_dt;
+    p.Pm = q.c0 * a.dt_f;
+    p.Qm = fmaf(q.c1, a.dt_f, 1.0f);
+    p.Sm = q.sigma * a.sqrt_dt_f;
   }
 }
 
 template <int kMode>
 __device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimArgs& a) {
-  p.h = (typename Types<kMode>::H)a.dt;
+  if constexpr (kMode == kModeF32) p.h = a.dt_f;
+  else p.h = a.dt;
   if constexpr (kMode != kModeF64) {
     p.P = p.Pm;
     p.Q = p.Qm;
@@ -280,7 +303,9 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
     p.S = g.e64[p.e].sigma * sqrt(p.h);
   } else {
     const EdgeRec32& q = g.e32[p.e];
-    const float hf = (float)p.h;
+    float hf;
+    if constexpr (kMode == kModeMixed) hf = narrow_f64_rn(p.h);
+    else hf = p.h;
     float rh;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(hf));
     p.P = q.c0 * hf;
@@ -421,7 +446,6 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
                                       const typename Types<kMode>::R* ring, uint32_t pid,
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
-  using H = typename Types<kMode>::H;
   p.pending = false;
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
@@ -430,6 +454,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
       p.wor);
   const bool hit_init = !(sub_step_end(p, Wp) > R(0));
   int32_t v;
+  bool rest;  // time is left in the step after this hit
   if constexpr (kMode == kModeF64) {
     const double mu = p.c0 + p.c1 * xs;
     const double a_ = mu * p.h;
@@ -441,11 +466,14 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     const double alpha = s * s;
     p.h = (1.0 - alpha) * p.h;
     if (p.h < 1e-9 * a.dt) p.flags |= 1u;
+    rest = p.h > 0.0;
     v = hit_init ? g.e64[p.e].src : g.e64[p.e].dst;
   } else {
     // increments of the pending sub-step in binary32: a = mu(x) h, b = S W
     const EdgeRec32& q = g.e32[p.e];
-    const float hf = (float)p.h;
+    float hf;
+    if constexpr (kMode == kModeMixed) hf = narrow_f64_rn(p.h);
+    else hf = p.h;
     const float a_ = fmaf(q.c1, xs, q.c0) * hf;
     const float b_ = p.S * Wp;
     const float A = hit_init ? a_ : -a_;
@@ -453,11 +481,18 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     const float C = hit_init ? xs : p.L - xs;
     const float s = hit_root_fast(A, B, C);
     if constexpr (kMode == kModeMixed) {
-      const double sd = (double)s;
-      const double alpha = sd * sd;   // binary64 hitting fraction
-      p.h = fma(-alpha, p.h, p.h);    // binary64 time left
+      // binary64 hitting fraction and time left; below 2^-60, alpha = s^2 <
+      // 2^-120 leaves h unchanged in binary64
+      if (s >= 0x1p-60f) {
+        const double sd = widen_unit_f32(s);
+        const double alpha = sd * sd;
+        p.h = fma(-alpha, p.h, p.h);
+      }
+      // h(1 - alpha) > 0 exactly when s < 1, and stays positive when rounded
+      rest = s < 1.0f;
     } else {
       p.h = fmaf(-s * s, p.h, p.h);
+      rest = p.h > 0.0f;
     }
     v = hit_init ? q.src : q.dst;
   }
@@ -480,7 +515,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   p.at_v = true;
   p.cur_slot = slot;
   set_vertex_sign(p, sr.end);
-  if (p.k == a.M || !(p.h > (H)0)) {  // the step ends at the vertex
+  if (p.k == a.M || !rest) {  // the step ends at the vertex
     if (p.k == a.M) trunc++;
     p.k = 0;
     p.in_cont = false;

@@ -90,6 +90,7 @@ struct SimArgs {
   uint32_t instance;
   int64_t steps;
   double dt, sqrt_dt;
+  float dt_f, sqrt_dt_f;  // the same rounded to binary32 (binary32 coefficients)
   int32_t M;
   int32_t hist_bins;    // 0: no fused histogram
   uint32_t* hist;       // [E * hist_bins]
