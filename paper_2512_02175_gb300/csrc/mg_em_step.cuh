@@ -402,38 +402,41 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
 
 // Up to kSub interior sub-steps over whole steps (h = dt, W = z), stopping
 // at the first that ends outside (0, l_e) -- the lane is then pending -- or,
-// with kCheckLeft, when the launch's steps are done.
+// with kCheckLeft, when the launch's steps are done.  Branch-free: every
+// unrolled sub-step is evaluated and a running "all inside so far" predicate
+// decides which ones count.  Ring rows past the lane's generated normals may
+// be read (in bounds: at most kRing - 1 + kSub - 1 < 2 kRing) but never count.
 template <int kMode, bool kCheckLeft>
 __device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Types<kMode>::R* ring,
                                               bool run) {
   using R = typename Types<kMode>::R;
+  constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
   const R* r = ring + (p.n_draw & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x;
-  uint32_t used = 0;
-  bool out = false;
+  const uint32_t lim = kCheckLeft ? (p.left < kSub ? p.left : kSub) : kSub;
+  uint32_t n_in = 0;
+  bool go = run;
 #pragma unroll
-  for (int q = 0; q < Types<kMode>::kSub; ++q) {
-    if (run) {
-      const R z = r[q * kThreads];
-      R xt;
-      if constexpr (kMode == kModeF64) {
-        const double mu = p.c0 + p.c1 * p.x;
-        const double a_ = mu * p.h;
-        const double b_ = p.S * z;
-        xt = p.x + a_ + b_;
-        mark_near_branch(p, xt);
-      } else {
-        xt = fmaf(p.Sm, z, fmaf(p.x, p.Qm, p.Pm));
-      }
-      const bool in = (xt > R(0)) & (xt < p.L);
-      p.x = in ? xt : p.x;
-      used = q + 1;
-      out = !in;
-      run = in;
-      if constexpr (kCheckLeft) run = run && ((uint32_t)(q + 1) < p.left);
+  for (int q = 0; q < (int)kSub; ++q) {
+    const bool att = go && (!kCheckLeft || (uint32_t)q < lim);
+    const R z = r[q * kThreads];
+    R xt;
+    if constexpr (kMode == kModeF64) {
+      const double mu = p.c0 + p.c1 * p.x;
+      const double a_ = mu * p.h;
+      const double b_ = p.S * z;
+      xt = p.x + a_ + b_;
+      if (att) mark_near_branch(p, xt);
+    } else {
+      xt = fmaf(p.Sm, z, fmaf(p.x, p.Qm, p.Pm));
     }
+    const bool in = att & (xt > R(0)) & (xt < p.L);
+    p.x = in ? xt : p.x;
+    n_in += in ? 1u : 0u;
+    go = in;
   }
-  p.n_draw += used;
-  p.left -= used - (out ? 1u : 0u);
+  const bool out = run && n_in < lim;
+  p.n_draw += n_in + (out ? 1u : 0u);
+  p.left -= n_in;
   p.pending = p.pending | out;
   if (p.left == 0u) p.active = false;
 }
