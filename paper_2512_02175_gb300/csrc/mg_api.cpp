@@ -237,14 +237,33 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
               g->slot_of_end[2 * (size_t)e + 1]};
   }
   std::vector<mg::SlotRec> slots(S);
-  for (int32_t j = 0; j < S; ++j) slots[j] = {g->slot_T[j], g->slot_edge[j], g->slot_end[j]};
+  for (int32_t j = 0; j < S; ++j)
+    slots[j] = {g->slot_T[j] ? (uint32_t)(g->slot_T[j] - 1u) : 0u, g->slot_edge[j],
+                g->slot_end[j], 0};
+  // Guide tables: vertex v with d slots gets 2^gb entries (2^gb >= d); entry
+  // k is the first slot whose threshold exceeds k 2^(32 - gb).  Thresholds are
+  // non-decreasing and the last is 2^32, so every entry is a slot of v.
   std::vector<mg::VtxRec> vtx(V);
-  for (int32_t v = 0; v < V; ++v) vtx[v] = {g->vtx_off[v], g->vtx_off[v + 1], g->kind[v], 0};
+  std::vector<int32_t> guide;
+  for (int32_t v = 0; v < V; ++v) {
+    const int32_t lo = g->vtx_off[v], hi = g->vtx_off[v + 1];
+    int gb = 0;
+    while ((1 << gb) < hi - lo) ++gb;
+    vtx[v] = {lo, hi, g->kind[v], (int32_t)guide.size()};
+    int32_t j = lo;
+    for (int64_t k = 0; k < (int64_t(1) << gb); ++k) {
+      const uint64_t bucket_lo = (uint64_t)k << (32 - gb);
+      while (j < hi - 1 && g->slot_T[j] <= bucket_lo) ++j;
+      guide.push_back(j);
+    }
+  }
+  const int32_t G = (int32_t)guide.size();
 
   const size_t o32 = 0, o64 = a256(o32 + E * sizeof(mg::EdgeRec32));
   const size_t os = a256(o64 + E * sizeof(mg::EdgeRec64));
   const size_t ov = a256(os + S * sizeof(mg::SlotRec));
-  const size_t orr = a256(ov + V * sizeof(mg::VtxRec));
+  const size_t og = a256(ov + V * sizeof(mg::VtxRec));
+  const size_t orr = a256(og + (size_t)G * sizeof(int32_t));
   const size_t total = a256(orr + E * sizeof(double));
   mg_status st = dev_alloc(g->buf, total, nullptr);
   if (st != MG_OK) {
@@ -256,6 +275,7 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   memcpy(host.data() + o64, e64.data(), E * sizeof(mg::EdgeRec64));
   memcpy(host.data() + os, slots.data(), S * sizeof(mg::SlotRec));
   memcpy(host.data() + ov, vtx.data(), V * sizeof(mg::VtxRec));
+  memcpy(host.data() + og, guide.data(), (size_t)G * sizeof(int32_t));
   memcpy(host.data() + orr, g->range.data(), E * sizeof(double));
   cudaError_t ce = cudaMemcpy(g->buf.p, host.data(), total, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
@@ -271,6 +291,8 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   g->view.e64 = reinterpret_cast<const mg::EdgeRec64*>(base + o64);
   g->view.slot = reinterpret_cast<const mg::SlotRec*>(base + os);
   g->view.vtx = reinterpret_cast<const mg::VtxRec*>(base + ov);
+  g->view.G = G;
+  g->view.guide = reinterpret_cast<const int32_t*>(base + og);
   g->view.range = reinterpret_cast<const double*>(base + orr);
   *out = g;
   return MG_OK;
@@ -526,7 +548,7 @@ struct Plan {
   bool f64 = false, stage = true, counters = true, shist = false;
   int32_t hist_len = 0;
   size_t smem(bool with_hist, const mg_graph g) const {
-    return mg::smem_layout(g->V, g->E, g->S, f64, stage, counters,
+    return mg::smem_layout(g->V, g->E, g->S, g->view.G, f64, stage, counters,
                            (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
   }
 };
@@ -554,8 +576,10 @@ Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32
   pl.hist_len = hist_bins > 0 ? g->E * hist_bins : 0;
   pl.shist = hist_bins > 0;
   const size_t budget = kSmemBudget + 128u * mg::kBlock;  // + the normal ring
-  const size_t tables = mg::smem_layout(g->V, g->E, g->S, pl.f64, true, false, 0, mg::kBlock).total -
-                        mg::smem_layout(g->V, g->E, g->S, pl.f64, false, false, 0, mg::kBlock).total;
+  const int32_t G = g->view.G;
+  const size_t tables =
+      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, true, false, 0, mg::kBlock).total -
+      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, false, false, 0, mg::kBlock).total;
   if (tables > stage_limit) pl.stage = false;
   if (pl.smem(true, g) > budget) pl.shist = false;
   if (pl.smem(true, g) > budget) pl.counters = false;

@@ -158,37 +158,33 @@ __device__ __forceinline__ T hit_root(T A, T B, T C) {
 }
 
 // The same root in binary32 with the hardware's approximate reciprocal and
-// square root (a few ulp; the result is clamped to [0, 1] all the same).
+// square root (a few ulp; the result is clamped to [0, 1] all the same),
+// branch-free: one quotient num / den picks the side's cancellation-free
+// form.  For A = 0, d = |B| and the B <= 0 form is 2C / (2|B|) = -C/B, while
+// B > 0 gives a zero denominator (no root in [0, 1]); den = 0 gives 0.
 __device__ __forceinline__ float hit_root_fast(float A, float B, float C) {
-  float s;
-  if (A == 0.0f) {
-    s = (B == 0.0f) ? 0.0f : __fdividef(-C, B);
-  } else {
-    const float disc = fmaf(B, B, -4.0f * A * C);
-    float d;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(d) : "f"(fmaxf(disc, 0.0f)));
-    if (B > 0.0f) {
-      s = __fdividef(-B - d, 2.0f * A);
-    } else {
-      const float den = -B + d;
-      s = (den == 0.0f) ? 0.0f : __fdividef(2.0f * C, den);
-    }
-  }
-  if (!(s > 0.0f)) s = 0.0f;
-  if (s > 1.0f) s = 1.0f;
-  return s;
+  const float disc = fmaf(B, B, -4.0f * A * C);
+  float d;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(d) : "f"(fmaxf(disc, 0.0f)));
+  const bool pos = B > 0.0f;
+  const float num = pos ? -B - d : 2.0f * C;
+  const float den = pos ? 2.0f * A : d - B;
+  float s = __fdividef(num, den);
+  if (!(s > 0.0f) || den == 0.0f) s = 0.0f;  // negative, NaN, or no root
+  return fminf(s, 1.0f);
 }
 
 // Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j
-// (thresholds are non-decreasing and the last is 2^32 > u).
+// (thresholds are non-decreasing and the last is 2^32 > u).  The guide entry
+// of u's bucket is that j or an earlier slot of v (every slot before it has
+// T_j <= the bucket's lower end <= u), so a forward scan from it finds j; it
+// stops at the last slot at the latest (tm1 = 2^32 - 1 >= u).
 __device__ __forceinline__ int32_t choose_slot(const GraphView& g, const VtxRec& vr, uint32_t u) {
-  int32_t lo = vr.begin, hi = vr.end - 1;
-  while (lo < hi) {
-    const int32_t mid = (lo + hi) >> 1;
-    if ((uint64_t)u < g.slot[mid].T) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
+  const int32_t d = vr.end - vr.begin;
+  const uint32_t gb = (d > 1) ? 32u - (uint32_t)__clz(d - 1) : 0u;  // 2^gb >= d
+  int32_t j = g.guide[vr.guide + (int32_t)__funnelshift_l(u, 0u, gb)];  // u >> (32 - gb)
+  while (u > g.slot[j].tm1) ++j;
+  return j;
 }
 
 struct BlockCounters {
@@ -248,6 +244,7 @@ struct Lane {
   R Pm, Qm, Sm;  // the same for a whole step (h = dt)
   R c0, c1;      // binary64 mode
   H h;           // time left in the current step
+  float hf;      // binary32-mixed mode: h rounded to binary32
   uint32_t wand, wor;
   int32_t cur_slot;  // slot of the vertex end the particle sits at
   int32_t k;         // splits in the current step
@@ -289,6 +286,7 @@ template <int kMode>
 __device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimArgs& a) {
   if constexpr (kMode == kModeF32) p.h = a.dt_f;
   else p.h = a.dt;
+  if constexpr (kMode == kModeMixed) p.hf = a.dt_f;
   if constexpr (kMode != kModeF64) {
     p.P = p.Pm;
     p.Q = p.Qm;
@@ -296,16 +294,21 @@ __device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimA
   p.S = p.Sm;
 }
 
-// Coefficients of a sub-step over the time left h on the current edge.
+// Coefficients of a sub-step over the time left h on the current edge (its
+// record q, already loaded, in the binary32 modes).
 template <int kMode>
-__device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const GraphView& g) {
+__device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const GraphView& g,
+                                                      const EdgeRec32& q) {
   if constexpr (kMode == kModeF64) {
     p.S = g.e64[p.e].sigma * sqrt(p.h);
   } else {
-    const EdgeRec32& q = g.e32[p.e];
     float hf;
-    if constexpr (kMode == kModeMixed) hf = narrow_f64_rn(p.h);
-    else hf = p.h;
+    if constexpr (kMode == kModeMixed) {
+      p.hf = narrow_f64_rn(p.h);
+      hf = p.hf;
+    } else {
+      hf = p.h;
+    }
     float rh;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(hf));
     p.P = q.c0 * hf;
@@ -475,7 +478,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     // increments of the pending sub-step in binary32: a = mu(x) h, b = S W
     const EdgeRec32& q = g.e32[p.e];
     float hf;
-    if constexpr (kMode == kModeMixed) hf = narrow_f64_rn(p.h);
+    if constexpr (kMode == kModeMixed) hf = p.hf;
     else hf = p.h;
     const float a_ = fmaf(q.c1, xs, q.c0) * hf;
     const float b_ = p.S * Wp;
@@ -513,7 +516,17 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   const U4 w = philox4x32_10(j, pid, 1u, a.instance, keys.rk);
   const int32_t slot = choose_slot(g, vr, w.x);
   const SlotRec sr = g.slot[slot];
-  enter_edge<kMode>(p, g, sr.edge, a);
+  EdgeRec32 qn{};  // the new edge (binary32 modes)
+  if constexpr (kMode == kModeF64) {
+    enter_edge<kMode>(p, g, sr.edge, a);
+  } else {
+    p.e = sr.edge;
+    qn = g.e32[sr.edge];
+    p.L = qn.L;
+    p.Pm = qn.c0 * a.dt_f;
+    p.Qm = fmaf(qn.c1, a.dt_f, 1.0f);
+    p.Sm = qn.sigma * a.sqrt_dt_f;
+  }
   p.x = (sr.end == kEndInit) ? R(0) : p.L;
   p.at_v = true;
   p.cur_slot = slot;
@@ -527,7 +540,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     return;
   }
   p.in_cont = true;
-  use_rest_coefficients(p, g);
+  use_rest_coefficients(p, g, qn);
 }
 
 // Histogram bin of position x on edge e (the set's precision):
@@ -546,11 +559,13 @@ __device__ __forceinline__ int32_t hist_bin(R x, double range, int32_t bins) {
   return b;
 }
 
+// Copies n elements in 16-byte pieces, rounding the byte count up to a
+// multiple of 16: both sides are padded to 16 bytes (the device tables to 256).
 template <typename T>
 __device__ __forceinline__ void block_copy(T* dst, const T* src, int32_t n) {
   const int4* s = reinterpret_cast<const int4*>(src);
   int4* d = reinterpret_cast<int4*>(dst);
-  const int32_t n16 = (int32_t)(((size_t)n * sizeof(T)) / 16);
+  const int32_t n16 = (int32_t)(((size_t)n * sizeof(T) + 15) / 16);
   for (int32_t k = threadIdx.x; k < n16; k += blockDim.x) d[k] = s[k];
 }
 
@@ -570,7 +585,7 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
   constexpr bool kF64 = kMode == kModeF64;
   GraphView g = a.g;
   const int32_t hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
-  const SmemLayout lay = smem_layout(g.V, g.E, g.S, kF64, a.stage_smem, a.smem_counters,
+  const SmemLayout lay = smem_layout(g.V, g.E, g.S, g.G, kF64, a.stage_smem, a.smem_counters,
                                      hist_len, kThreads);
   if (a.stage_smem) {
     if constexpr (kF64) {
@@ -582,8 +597,10 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
     }
     block_copy(reinterpret_cast<SlotRec*>(smem + lay.slots), g.slot, g.S);
     block_copy(reinterpret_cast<VtxRec*>(smem + lay.vtx), g.vtx, g.V);
+    block_copy(reinterpret_cast<int32_t*>(smem + lay.guide), g.guide, g.G);
     g.slot = reinterpret_cast<const SlotRec*>(smem + lay.slots);
     g.vtx = reinterpret_cast<const VtxRec*>(smem + lay.vtx);
+    g.guide = reinterpret_cast<const int32_t*>(smem + lay.guide);
   }
   BlockCounters bc{nullptr, nullptr};
   if (a.smem_counters) {

@@ -34,25 +34,32 @@ struct alignas(16) EdgeRec64 {
 };
 
 // One (vertex, incident edge end) with its integer jump threshold T in
-// [0, 2^32]: slot j of v is drawn when u < T_j and u >= T_{j-1}.
+// [0, 2^32]: slot j of v is drawn when u < T_j and u >= T_{j-1}.  Stored as
+// tm1 = T - 1 (so u < T is u <= tm1 in 32 bits); slots with T = 0 (zero
+// weight ahead of every positive one) hold 0 and are never compared, since
+// the guide table below never points at them.
 struct alignas(16) SlotRec {
-  uint64_t T;
-  int32_t edge, end;
+  uint32_t tm1;
+  int32_t edge, end, pad;
 };
 
-// Slots of vertex v are [begin, end); kind is mg_vertex_kind.
+// Slots of vertex v are [begin, end); kind is mg_vertex_kind.  guide: offset
+// of v's guide table (Chen and Asau, 1974) of 2^gb entries, gb the smallest
+// with 2^gb >= end - begin: entry k is the first slot j with T_j > k 2^(32-gb),
+// so the slot drawn by u is found by a forward scan from entry u >> (32 - gb).
 struct alignas(16) VtxRec {
-  int32_t begin, end, kind, pad;
+  int32_t begin, end, kind, guide;
 };
 
 // Read-only view of a graph on the device (global memory, or shared memory
 // after staging).
 struct GraphView {
-  int32_t V, E, S;
+  int32_t V, E, S, G;  // G: guide table entries of all vertices
   const EdgeRec32* e32;
   const EdgeRec64* e64;
   const SlotRec* slot;
   const VtxRec* vtx;
+  const int32_t* guide;
   const double* range;  // histogram range per edge
 };
 
@@ -103,14 +110,13 @@ struct SimArgs {
 // Dynamic shared memory of the fused kernel: staged tables, privatised
 // counters, privatised histogram (each part optional).
 struct SmemLayout {
-  size_t ring, edges, slots, vtx, exits, absorbed, hist, total;
+  size_t ring, edges, slots, vtx, guide, exits, absorbed, hist, total;
 };
 
 MG_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
-                                                  bool stage, bool counters, int32_t hist_len,
-                                                  int32_t block) {
+MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, int32_t G, bool f64,
+                                    bool stage, bool counters, int32_t hist_len, int32_t block) {
   SmemLayout l{};
   size_t off = 0;
   l.ring = off;  // buffered normals, each stored twice: 32 KB at 256 threads
@@ -119,6 +125,7 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, bool f64,
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));
     l.vtx = off; off += align16((size_t)V * sizeof(VtxRec));
+    l.guide = off; off += align16((size_t)G * sizeof(int32_t));
   }
   if (counters) {
     l.exits = off; off += align16((size_t)S * 4);
