@@ -7,8 +7,8 @@ L_e], sigma = sqrt(2), equal jump weights, reflecting leaves -- with
 N = 2^24 particles, dt = 1e-3, M = 16 splits per step at most, FP32-mixed,
 and a fused 32-bin-per-edge snapshot histogram.  One benchmark step is one
 mg_simulate call of 10^4 EM-Steps over all particles (one kernel launch) on
-device-resident state.  The state (N x 20 bytes = 335 MB) is larger than L2,
-so no explicit flush is needed between steps.
+device-resident state.  The state (N x 24 bytes = 403 MB) is larger than L2
+(129 MB), so no explicit flush is needed between steps.
 
 Printed: one JSON line (rank 0).  ``value`` is device-timed (CUDA events on
 the launch stream); ``e2e`` times the same work through the C ABI with host
@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--em-steps", type=int, default=EM_STEPS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hist", action="store_true",
+                    help="time the EM-Steps without the fused histogram tail")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="batch512: scale every instance's particle count by this factor")
     ap.add_argument("--cpu-sample", type=int, default=16_384)
     ap.add_argument("--workload", default="star16_langevin",
                     choices=["star16_langevin", "vascular", "batch512", "served"],
@@ -72,10 +76,13 @@ def config(args, world):
     return {"workload": "star16_langevin", "graph": "star, 16 edges, L~U[0.5,2], quadratic "
             "potentials, sigma=sqrt(2), equal b, reflecting leaves",
             "n_particles_per_gpu": args.n, "global_particles": args.n * world,
-            "dt": DT, "em_steps_per_step": args.em_steps, "M": M, "hist_bins_per_edge": BINS,
+            "dt": DT, "em_steps_per_step": args.em_steps, "M": M,
+            "hist_bins_per_edge": 0 if args.no_hist else BINS,
             "precision": {"mixed": "fp32 with fp64 hitting fraction and time left",
                           "fp32": "fp32", "fp64": "fp64"}[args.precision],
-            "parallelism": f"particle shards x{world}", "l2": "state 20 B/particle > L2"}
+            "parallelism": f"particle shards x{world}",
+            "l2": f"state {28 if args.precision == 'fp64' else 24} B/particle x N > L2 (129 MB): "
+                  "no flush needed"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -244,8 +251,11 @@ def run_ours(args):
     hist = torch.zeros(g.n_edges * BINS, dtype=torch.int32, device="cuda")
 
     def step():
-        hist.zero_()
-        p.simulate(DT, args.em_steps, M, BINS, hist, stream)
+        if args.no_hist:
+            p.simulate(DT, args.em_steps, M, 0, None, stream)
+        else:
+            hist.zero_()
+            p.simulate(DT, args.em_steps, M, BINS, hist, stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -332,6 +342,7 @@ def run_ours(args):
             "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk,
+            "nominal_particle_steps_per_s": n * world * args.em_steps * args.steps / elapsed,
             "launch_ms": launch_ms,
             "truncations": counts["truncations"],
         }
@@ -360,7 +371,8 @@ def run_vascular(args):
     from paper_2512_02175_gb300 import binding as B
     d = W.vascular()
     n = 1 << 26 if args.n == (1 << 24) else args.n
-    steps, Mv, bins = 2000, 32, 16
+    steps = 2000 if args.em_steps == EM_STEPS else args.em_steps
+    Mv, bins = 32, 16
     e0, x0 = W.inject_at_inlets(d, n, 11)
     B.load()
     B.use_torch_allocator()
@@ -416,7 +428,7 @@ def run_batch512(args):
     from paper_2512_02175_gb300 import binding as B
     B.load()
     B.use_torch_allocator()
-    insts = W.batch_instances(512)
+    insts = W.batch_instances(512, n_scale=args.scale)
     prec = _mode(B, args.precision)
     graphs, parts = [], []
     for k, it in enumerate(insts):
@@ -469,7 +481,8 @@ def run_batch512(args):
            "config": {"workload": "batch512", "instances": n_members, "work_items": n_items,
                       "persistent_blocks": blocks, "particles": int(sum(i["n"] for i in insts)),
                       "particle_steps_per_step": int(sum(i["n"] * i["steps"] for i in insts)),
-                      "cuda_graph": True, "tuning": tun.as_dict(), "precision": args.precision},
+                      "cuda_graph": True, "tuning": tun.as_dict(), "precision": args.precision,
+                      "particle_scale": args.scale},
            "launch_ms": ms}
     b.close()
     for p in parts:

@@ -185,6 +185,20 @@ mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t s
 mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
                       int32_t hist_bins, uint32_t* hist_out, void* stream);
 
+/* Time-averaged occupancy.  Section 5.1 estimates a steady-state density by a
+ * histogram of the particles after a long run; averaging snapshots over time
+ * lowers its noise.  Advances every particle by `steps` EM-Steps exactly as
+ * mg_simulate does (bit-identical results) and ADDS the snapshot histogram of
+ * the positions after every `every` EM-Steps -- steps / every snapshots, the
+ * last after step (steps / every) * every; a remainder runs without one -- to
+ * the device array hist_out[n_edges * hist_bins] (uint32, caller-zeroed;
+ * bins as mg_histogram).  Divided by (snapshots x living particles) it is the
+ * occupancy averaged over those times.  A bin must stay below 2^32 counts
+ * (snapshots x n < 2^32 suffices).  every >= 1, hist_bins >= 1, hist_out
+ * non-NULL; otherwise as mg_simulate.  Stream-ordered. */
+mg_status mg_simulate_sampled(mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
+                              int64_t every, int32_t hist_bins, uint32_t* hist_out, void* stream);
+
 /* ---------------------------------------------------------------- batches
  *
  * A batch advances many particle sets (instances: different graphs, sizes,

@@ -55,6 +55,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 SYMBOLS = [
     "mg_set_allocator", "mg_graph_create", "mg_graph_destroy", "mg_graph_info", "mg_graph_slots",
     "mg_particles_init", "mg_particles_reset", "mg_particles_destroy", "mg_particles_set_tuning",
+    "mg_simulate_sampled",
     "mg_simulate",
     "mg_synchronize", "mg_histogram", "mg_histogram_static", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
     "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
@@ -101,6 +102,7 @@ def _declare(L):
         "mg_particles_destroy": ([vp], st),
         "mg_particles_set_tuning": ([vp, i32, i64], st),
         "mg_simulate": ([vp, dbl, i64, i32, i32, vp, vp], st),
+        "mg_simulate_sampled": ([vp, dbl, i64, i32, i64, i32, vp, vp], st),
         "mg_synchronize": ([vp], st),
         "mg_histogram": ([vp, i32, vp, C.c_int, vp], st),
         "mg_histogram_static": ([vp, i32, vp, vp], st),
@@ -283,6 +285,11 @@ def mg_particles_info(p):
 def mg_simulate(p, dt, steps, M, hist_bins=0, hist_out=None, stream=None):
     _check(load().mg_simulate(p, float(dt), int(steps), int(M), int(hist_bins), _ptr(hist_out),
                               _stream_ptr(stream)))
+
+
+def mg_simulate_sampled(p, dt, steps, M, every, hist_bins, hist_out, stream=None):
+    _check(load().mg_simulate_sampled(p, float(dt), int(steps), int(M), int(every),
+                                      int(hist_bins), _ptr(hist_out), _stream_ptr(stream)))
 
 
 def mg_synchronize(p):
@@ -469,6 +476,9 @@ class Particles:
 
     def simulate(self, dt, steps, M, hist_bins=0, hist_out=None, stream=None):
         mg_simulate(self.h, dt, steps, M, hist_bins, hist_out, stream)
+
+    def simulate_sampled(self, dt, steps, M, every, hist_bins, hist_out, stream=None):
+        mg_simulate_sampled(self.h, dt, steps, M, every, hist_bins, hist_out, stream)
 
     def synchronize(self):
         mg_synchronize(self.h)

@@ -642,6 +642,24 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   return MG_OK;
 }
 
+extern "C" mg_status mg_simulate_sampled(mg_particles p, double dt, int64_t steps, int32_t M,
+                                         int64_t every, int32_t hist_bins, uint32_t* hist_out,
+                                         void* stream) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "mg_simulate_sampled: NULL particles");
+  if (every < 1) return fail(MG_ERR_INVALID_ARG, "every must be >= 1");
+  if (hist_bins < 1 || !hist_out)
+    return fail(MG_ERR_INVALID_ARG, "mg_simulate_sampled needs hist_bins >= 1 and hist_out");
+  mg_status s = check_step_args(dt, steps, M, hist_bins, hist_out);
+  if (s != MG_OK) return s;
+  const int64_t snaps = steps / every;
+  for (int64_t k = 0; k < snaps; ++k) {
+    s = mg_simulate(p, dt, every, M, hist_bins, hist_out, stream);
+    if (s != MG_OK) return s;
+  }
+  const int64_t rest = steps - snaps * every;
+  return rest > 0 ? mg_simulate(p, dt, rest, M, 0, nullptr, stream) : MG_OK;
+}
+
 // ------------------------------------------------------------------ batches
 
 struct mg_batch_s {

@@ -1,0 +1,175 @@
+"""The paper's star experiment (Section 5.1 and the appendix's steady-state
+normalisers): five semi-infinite edges glued at one vertex, b = 1/5,
+sigma = 1 (D = sigma^2 / 2 = 1/2), drift towards the vertex
+mu_i = -10 i (linear potential) or mu_i = -10 i x (quadratic potential).
+
+The steady state is exponential (linear) or half-Gaussian (quadratic) on
+every edge with one normaliser B for all edges (continuity at the vertex;
+the printed formulas read with |mu_i|, reading R10):
+
+    linear     rho_i(x) = B exp(-|mu_i| x / D),      B = 1 / (D sum_i 1/|mu_i|)
+    quadratic  rho_i(x) = B exp(-|k_i| x^2 / (2D)),  B = sqrt(2 / (pi D)) / sum_i |k_i|^(-1/2)
+
+The density is estimated, as in the paper, by a histogram of the particles
+after a long run -- here averaged over snapshots (mg_simulate_sampled) --
+and scored by its L2 distance to the exact density.  The error must fall
+as dt falls and as N grows, the binary32-mixed path must score like the
+binary64 one, and the sampled histogram must equal a sum of snapshots.
+The printed table is the experiment's result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_02175_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+K, SIGMA, BINS = 5, 1.0, 64
+D = SIGMA * SIGMA / 2.0
+T_BURN, T_AVG, N_SNAP = 2.0, 1.0, 100
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    return B
+
+
+def rates(kind):
+    return 10.0 * np.arange(1, K + 1)          # |mu_i| (linear) or |k_i| (quadratic)
+
+
+def hist_range(kind):
+    """Histogram range per edge: 12 decay lengths (linear) or 5 standard
+    deviations (quadratic); the last bin also collects the tail beyond."""
+    r = rates(kind)
+    return 12.0 * D / r if kind == "linear" else 5.0 * np.sqrt(D / r)
+
+
+def exact_bin_mass(kind):
+    """Exact probability of each bin [x0, x1) of each edge under the steady
+    state; the last bin of an edge takes [x0, inf), as the histogram clamps."""
+    r = rates(kind)
+    out = np.zeros((K, BINS))
+    for i in range(K):
+        edges = np.linspace(0.0, hist_range(kind)[i], BINS + 1)
+        edges[-1] = np.inf
+        if kind == "linear":
+            Bn = 1.0 / (D * np.sum(1.0 / r))
+            a = r[i] / D
+            cdf = lambda x: Bn / a * (1.0 - np.exp(-a * x))
+        else:
+            Bn = math.sqrt(2.0 / (math.pi * D)) / np.sum(1.0 / np.sqrt(r))
+            s = math.sqrt(r[i] / (2.0 * D))
+            from scipy.special import erf
+            cdf = lambda x: Bn * math.sqrt(math.pi * D / (2.0 * r[i])) * erf(s * x)
+        c = np.array([cdf(x) if np.isfinite(x) else cdf(1e300) for x in edges])
+        out[i] = np.diff(c)
+    return out
+
+
+def l2_error(kind, counts, total):
+    """L2 distance between the histogram density estimate and the exact
+    density: sqrt(sum over bins of (p_hat - p)^2 / dx), p = bin mass.  The
+    open last bin is left out (its width is not dx)."""
+    p_hat = counts.reshape(K, BINS) / total
+    p = exact_bin_mass(kind)
+    err = 0.0
+    for i in range(K):
+        dx = hist_range(kind)[i] / BINS
+        err += np.sum((p_hat[i, :-1] - p[i, :-1]) ** 2) / dx
+    return math.sqrt(err)
+
+
+def run(B, kind, n, dt, prec=None, seed=3):
+    import torch
+    d = W.paper_star(kind, k=K, sigma=SIGMA, hist_range=hist_range(kind))
+    r = np.random.Generator(np.random.PCG64(seed))
+    e = (np.arange(n) % K).astype(np.int32)
+    x = r.uniform(0.0, 1.0, n) * hist_range(kind)[e]
+    g = B.Graph(d)
+    p = B.Particles(g, e, x, seed=seed, precision=B.MG_FP32_MIXED if prec is None else prec)
+    burn = int(round(T_BURN / dt))
+    every = max(1, int(round(T_AVG / dt / N_SNAP)))
+    h = torch.zeros(K * BINS, dtype=torch.int32, device="cuda")
+    p.simulate(dt, burn, 64)
+    p.simulate_sampled(dt, every * N_SNAP, 64, every, BINS, h)
+    p.synchronize()
+    c = p.counts()
+    counts = h.cpu().numpy().astype(np.float64)
+    p.close()
+    g.close()
+    return l2_error(kind, counts, n * N_SNAP), int(c["truncations"]) / int(c["particle_steps"])
+
+
+@pytest.mark.parametrize("kind", ["linear", "quadratic"])
+def test_density_error_falls_with_dt_and_n(B, kind):
+    n = 1 << 20
+    dts = [4e-3, 1e-3, 2.5e-4, 6.25e-5]
+    sweep = [run(B, kind, n, dt) for dt in dts]
+    errs = [e for e, _ in sweep]
+    ns = [1 << 14, 1 << 17]
+    errs_n = [run(B, kind, m, 2.5e-4)[0] for m in ns] + [errs[2]]
+    e64 = run(B, kind, 1 << 18, 2.5e-4, prec=B.MG_FP64)[0]
+    e32 = run(B, kind, 1 << 18, 2.5e-4)[0]
+    norm = math.sqrt(sum(np.sum(pm[:-1] ** 2) / (hist_range(kind)[i] / BINS)
+                         for i, pm in enumerate(exact_bin_mass(kind))))
+    print(f"\n{kind} potential: L2 density error (relative to ||rho||_2 = {norm:.3f})")
+    print("  N = 2^20, dt sweep: " + ", ".join(
+        f"dt={dt:g}: {e:.4f} ({e / norm:.2%}; truncated steps {tr:.1e})"
+        for dt, (e, tr) in zip(dts, sweep)))
+    print("  dt = 2.5e-4, N sweep: " + ", ".join(f"N=2^{int(math.log2(m))}: {e:.4f}"
+                                               for m, e in zip(ns + [n], errs_n)))
+    print(f"  N = 2^18, dt = 2.5e-4: FP64 {e64:.4f}, FP32-mixed {e32:.4f}")
+    # the bias falls with dt (each quartering of dt lowers the error), and the
+    # finest setting is far below the coarsest
+    for a, b in zip(errs, errs[1:]):
+        assert b < a * 1.02
+    assert errs[-1] < 0.35 * errs[0]
+    if kind == "linear":
+        # drift into the vertex: the vertex bias dominates at every N here and
+        # falls like sqrt(dt) (Corollary 1's rate): quartering dt halves it
+        for a, b in zip(errs[1:], errs[2:]):
+            assert 1.6 < a / b < 2.5
+    else:
+        # drift vanishing at the vertex: the sampling error shows, and falls
+        # with N
+        assert errs_n[0] > 2.0 * errs_n[-1]
+    # binary32 positions with binary64 split arithmetic score like binary64
+    assert abs(e32 - e64) < 0.15 * e64 + 0.01 * norm
+
+
+def test_sampled_histogram_is_a_sum_of_snapshots(B):
+    """mg_simulate_sampled is mg_simulate in chunks of `every` steps with the
+    fused snapshot histogram added after each: bit-identical states, and a
+    histogram equal to the sum of the snapshots."""
+    import torch
+    d = W.paper_star("quadratic", k=K, sigma=SIGMA, hist_range=hist_range("quadratic"))
+    e = (np.arange(50_000) % K).astype(np.int32)
+    x = np.linspace(0.0, 0.3, 50_000)
+    g = B.Graph(d)
+    a = B.Particles(g, e, x, seed=4, precision=B.MG_FP32_MIXED)
+    b = B.Particles(g, e, x, seed=4, precision=B.MG_FP32_MIXED)
+    ha = torch.zeros(K * BINS, dtype=torch.int32, device="cuda")
+    hb = torch.zeros(K * BINS, dtype=torch.int32, device="cuda")
+    a.simulate_sampled(1e-3, 7 * 30 + 11, 16, 30, BINS, ha)
+    for _ in range(7):
+        b.simulate(1e-3, 30, 16, BINS, hb)
+    b.simulate(1e-3, 11, 16)
+    a.synchronize()
+    b.synchronize()
+    sa, sb = a.state(), b.state()
+    for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(ha.cpu().numpy(), hb.cpu().numpy())
+    assert int(ha.sum()) == 7 * 50_000
+    with pytest.raises(B.MGError):
+        a.simulate_sampled(1e-3, 10, 16, 0, BINS, ha)
+    a.close()
+    b.close()
+    g.close()
