@@ -415,6 +415,18 @@ void or_histogram(const or_graph* g, int64_t n, const int32_t* edge, const doubl
   }
 }
 
+void or_histogram_binned(const or_graph* g, int64_t n, const int32_t* edge, const double* x,
+                         const int32_t* off, const double* up, uint64_t* hist) {
+  (void)g;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t e = edge[i];
+    if (e == OR_DEAD || off[e] == off[e + 1]) continue;
+    int32_t j = off[e];
+    while (j < off[e + 1] - 1 && !(x[i] < up[j])) j++;
+    hist[j]++;
+  }
+}
+
 int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* n_draw,
                         uint32_t* hits, uint32_t* first_hits, uint32_t* flags, double dt,
                         int32_t M, const double* zs, int32_t n_z, const uint32_t* us,

@@ -142,6 +142,14 @@ void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edg
 void or_histogram(const or_graph* g, int64_t n, const int32_t* edge, const double* x,
                   int32_t B, uint64_t* hist);
 
+/* Snapshot histogram with bins of any width per edge (Section 5.1 estimates
+ * densities by histograms; the bins of edge e are off[e] .. off[e+1]-1 with
+ * upper boundaries up[j], increasing within the edge).  A living particle at
+ * x on e counts in the first bin j of e with x < up[j], else in e's last bin;
+ * an edge without bins counts nothing.  hist[off[E]] accumulates. */
+void or_histogram_binned(const or_graph* g, int64_t n, const int32_t* edge, const double* x,
+                         const int32_t* off, const double* up, uint64_t* hist);
+
 /* Test hook: one EM-Step of one particle with injected draws: the normals
  * zs[0..n_z) of its sub-steps in order, the u32s us[0..n_u) of its hits. */
 int or_em_step_injected(const or_graph* g, int32_t* edge, double* x, uint32_t* n_draw,

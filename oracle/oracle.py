@@ -86,6 +86,9 @@ def _declare(L):
     L.or_simulate.restype = None
     L.or_histogram.argtypes = [C.c_void_p, i64, _p(i32), _p(dbl), i32, _p(u64)]
     L.or_histogram.restype = None
+    L.or_histogram_binned.argtypes = [C.c_void_p, i64, _p(i32), _p(dbl), _p(i32), _p(dbl),
+                                      _p(u64)]
+    L.or_histogram_binned.restype = None
     L.or_em_step_injected.argtypes = [C.c_void_p, _p(i32), _p(dbl), _p(u32), _p(u32), _p(u32),
                                       _p(u32), dbl, i32, _p(dbl), i32, _p(u32), i32, _p(u64),
                                       _p(u64), _p(u64)]
@@ -242,6 +245,17 @@ def histogram(g: Graph, st: State, bins: int) -> np.ndarray:
     h = np.zeros(g.n_edges * bins, np.uint64)
     lib().or_histogram(g._h, len(st), _ptr(st.edge, C.c_int32), _ptr(st.x, C.c_double),
                        int(bins), _ptr(h, C.c_uint64))
+    return h
+
+
+def histogram_binned(g: Graph, st: State, offsets, upper) -> np.ndarray:
+    """Counts per variable-width bin: offsets[E+1] (int32), upper[offsets[E]]
+    (binary64 upper boundaries, increasing within an edge)."""
+    off = np.ascontiguousarray(offsets, np.int32)
+    up = np.ascontiguousarray(upper, np.float64)
+    h = np.zeros(int(off[-1]), np.uint64)
+    lib().or_histogram_binned(g._h, len(st), _ptr(st.edge, C.c_int32), _ptr(st.x, C.c_double),
+                              _ptr(off, C.c_int32), _ptr(up, C.c_double), _ptr(h, C.c_uint64))
     return h
 
 
