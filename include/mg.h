@@ -271,6 +271,23 @@ mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, int out_on_d
  * different streams or threads, race. */
 mg_status mg_histogram_static(mg_particles p, int32_t bins, uint32_t* out, void* stream);
 
+/* Snapshot histogram with bins of any width per edge (the paper's densities
+ * are histograms of the particles' positions, Section 5.1; here each edge
+ * takes its own bin boundaries).  bin_offsets[n_edges + 1] (host, int32):
+ * the bins of edge e are bin_offsets[e] .. bin_offsets[e+1]-1, bin_offsets[0]
+ * = 0, non-decreasing (an edge may have none); bin_upper[bin_offsets[n_edges]]
+ * (host, binary64): the bins' upper boundaries, finite, > 0 and strictly
+ * increasing within an edge.  A living particle at x on e counts in the first
+ * bin j of e with x < bin_upper[j] -- half-open bins, as the uniform bins of
+ * mg_histogram -- or in e's last bin when x is at or beyond every boundary;
+ * edges without bins and dead particles count nothing.  For binary32 states
+ * the boundaries are rounded up to binary32, which decides every comparison
+ * exactly as in binary64.  out[bin_offsets[n_edges]] (uint32) is overwritten:
+ * host memory (synchronises) or device memory (out_on_device != 0,
+ * stream-ordered).  MG_ERR_INVALID_ARG for malformed offsets or boundaries. */
+mg_status mg_histogram_binned(mg_particles p, const int32_t* bin_offsets, const double* bin_upper,
+                              uint32_t* out, int out_on_device, void* stream);
+
 /* Copies the set's counters to host arrays (synchronises): slot_exits[n_slots]
  * (in the slot order of mg_graph_slots), absorbed[n_vertices], truncations[1],
  * particle_steps[1] (steps taken by living particles).  Any pointer may be

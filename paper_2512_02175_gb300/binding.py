@@ -55,7 +55,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 SYMBOLS = [
     "mg_set_allocator", "mg_graph_create", "mg_graph_destroy", "mg_graph_info", "mg_graph_slots",
     "mg_particles_init", "mg_particles_reset", "mg_particles_destroy", "mg_particles_set_tuning",
-    "mg_simulate_sampled",
+    "mg_simulate_sampled", "mg_histogram_binned",
     "mg_simulate",
     "mg_synchronize", "mg_histogram", "mg_histogram_static", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
     "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
@@ -103,6 +103,7 @@ def _declare(L):
         "mg_particles_set_tuning": ([vp, i32, i64], st),
         "mg_simulate": ([vp, dbl, i64, i32, i32, vp, vp], st),
         "mg_simulate_sampled": ([vp, dbl, i64, i32, i64, i32, vp, vp], st),
+        "mg_histogram_binned": ([vp, vp, vp, vp, C.c_int, vp], st),
         "mg_synchronize": ([vp], st),
         "mg_histogram": ([vp, i32, vp, C.c_int, vp], st),
         "mg_histogram_static": ([vp, i32, vp, vp], st),
@@ -310,6 +311,21 @@ def mg_histogram(p, bins, out=None, stream=None):
     return out
 
 
+def mg_histogram_binned(p, bin_offsets, bin_upper, out, stream=None):
+    """Variable-width bins: bin_offsets int32 [E + 1], bin_upper float64
+    [bin_offsets[-1]]; fills ``out`` (numpy uint32 or a CUDA tensor) with the
+    counts (see include/mg.h)."""
+    off = np.ascontiguousarray(bin_offsets, np.int32)
+    up = np.ascontiguousarray(bin_upper, np.float64)
+    if len(up) != int(off[-1]):
+        raise ValueError("bin_upper must have bin_offsets[-1] entries")
+    dev = 1 if _on_device(out) else 0
+    if not dev and (out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]):
+        raise ValueError("host output must be a C-contiguous uint32 array")
+    _check(load().mg_histogram_binned(p, _ptr(off), _ptr(up), _ptr(out), dev, _stream_ptr(stream)))
+    return out
+
+
 def mg_histogram_static(p, bins, out, stream=None):
     """The snapshot histogram into the host array ``out`` (uint32 [E * bins])
     without any device allocation by the library (see include/mg.h)."""
@@ -487,6 +503,11 @@ class Particles:
         if out is None:
             out = np.zeros(self.graph.n_edges * bins, np.uint32)
         return mg_histogram(self.h, bins, out, stream)
+
+    def histogram_binned(self, bin_offsets, bin_upper, out=None, stream=None):
+        if out is None:
+            out = np.zeros(max(1, int(np.asarray(bin_offsets)[-1])), np.uint32)
+        return mg_histogram_binned(self.h, bin_offsets, bin_upper, out, stream)
 
     def counts(self, stream=None):
         return mg_exit_counts(self.h, self.graph.n_slots, self.graph.n_vertices, stream)

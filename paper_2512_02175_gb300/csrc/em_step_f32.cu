@@ -2,6 +2,7 @@
 // EM-Step kernel, the binary32 histogram kernel and the state initialisation
 // kernels.
 #include "mg_em_step.cuh"
+#include "mg_histogram.cuh"
 #include "mg_launch.h"
 
 namespace mg {
@@ -87,6 +88,41 @@ cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const 
     cudaFuncSetAttribute(histogram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sh);
   histogram_kernel<float><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram_binned_f32(const int32_t* edge, const void* x, int64_t n,
+                                        const int32_t* off, const float* up, int32_t n_bins,
+                                        uint32_t* out, cudaStream_t st);
+cudaError_t launch_histogram_binned_f64(const int32_t* edge, const void* x, int64_t n,
+                                        const int32_t* off, const double* up, int32_t n_bins,
+                                        uint32_t* out, cudaStream_t st);
+
+cudaError_t launch_histogram_binned(bool f64, const int32_t* edge, const void* x, int64_t n,
+                                    const int32_t* off, const void* up, int32_t n_bins,
+                                    uint32_t* out, cudaStream_t st) {
+  return f64 ? launch_histogram_binned_f64(edge, x, n, off, static_cast<const double*>(up), n_bins,
+                                           out, st)
+             : launch_histogram_binned_f32(edge, x, n, off, static_cast<const float*>(up), n_bins,
+                                           out, st);
+}
+
+cudaError_t launch_histogram_binned_f32(const int32_t* edge, const void* x, int64_t n,
+                                        const int32_t* off, const float* up, int32_t n_bins,
+                                        uint32_t* out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  const bool smem = (size_t)n_bins * 4 <= 96 * 1024;
+  const size_t sh = smem ? align16((size_t)n_bins * 4) : 0;
+  if (sh > 48 * 1024)
+    cudaFuncSetAttribute(histogram_binned_kernel<float>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  histogram_binned_kernel<float><<<(unsigned)grid, kBlock, sh, st>>>(edge, x, n, off, up, n_bins,
+                                                                     out, smem ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 // (--fmad=false) so that every binary64 operation rounds exactly as written,
 // in the same order as the plain CPU reference of the scheme.
 #include "mg_em_step.cuh"
+#include "mg_histogram.cuh"
 #include "mg_launch.h"
 
 namespace mg {
@@ -53,6 +54,25 @@ cudaError_t launch_histogram_f64(const GraphView& g, const int32_t* edge, const 
     cudaFuncSetAttribute(histogram_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sh);
   histogram_kernel<double><<<(unsigned)grid, kBlock, sh, st>>>(g, edge, x, n, bins, out, smem ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram_binned_f64(const int32_t* edge, const void* x, int64_t n,
+                                        const int32_t* off, const double* up, int32_t n_bins,
+                                        uint32_t* out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  const bool smem = (size_t)n_bins * 4 <= 96 * 1024;
+  const size_t sh = smem ? align16((size_t)n_bins * 4) : 0;
+  if (sh > 48 * 1024)
+    cudaFuncSetAttribute(histogram_binned_kernel<double>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  histogram_binned_kernel<double><<<(unsigned)grid, kBlock, sh, st>>>(edge, x, n, off, up, n_bins,
+                                                                      out, smem ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -341,6 +341,7 @@ struct mg_particles_s {
   DevBuf state;      // edge | x | n_draw | hits | first_hits | flags
   DevBuf counters;   // exits[S] | absorbed[V] | trunc | psteps | err
   DevBuf hist_tmp;   // histogram staging for host output
+  DevBuf bins_tmp;   // variable-width bin tables (offsets | boundaries)
   mg::StateView sv{};
   mg::CounterView cv{};
   cudaStream_t last_stream = nullptr;
@@ -479,6 +480,7 @@ extern "C" mg_status mg_particles_destroy(mg_particles p) {
   dev_free(p->state, p->last_stream);
   dev_free(p->counters, p->last_stream);
   dev_free(p->hist_tmp, p->last_stream);
+  dev_free(p->bins_tmp, p->last_stream);
   p->g->refs--;
   delete p;
   return MG_OK;
@@ -914,6 +916,70 @@ extern "C" mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, i
     MG_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
     MG_CUDA(cudaStreamSynchronize(st));
   }
+  return MG_OK;
+}
+
+extern "C" mg_status mg_histogram_binned(mg_particles p, const int32_t* bin_offsets,
+                                         const double* bin_upper, uint32_t* out,
+                                         int out_on_device, void* stream) {
+  if (!p || !bin_offsets || !out)
+    return fail(MG_ERR_INVALID_ARG, "mg_histogram_binned: NULL argument");
+  const mg_graph g = p->g;
+  if (bin_offsets[0] != 0) return fail(MG_ERR_INVALID_ARG, "bin_offsets[0] must be 0");
+  for (int32_t e = 0; e < g->E; ++e)
+    if (bin_offsets[e + 1] < bin_offsets[e])
+      return fail(MG_ERR_INVALID_ARG, "bin_offsets must be non-decreasing (edge %d)", e);
+  const int32_t nb = bin_offsets[g->E];
+  if (nb > 0 && !bin_upper) return fail(MG_ERR_INVALID_ARG, "mg_histogram_binned: NULL bin_upper");
+  for (int32_t e = 0; e < g->E; ++e)
+    for (int32_t j = bin_offsets[e]; j < bin_offsets[e + 1]; ++j) {
+      const double u = bin_upper[j];
+      const double prev = (j == bin_offsets[e]) ? 0.0 : bin_upper[j - 1];
+      if (!(std::isfinite(u) && u > prev))
+        return fail(MG_ERR_INVALID_ARG,
+                    "edge %d: bin boundaries must be finite, > 0 and increasing (bin %d)", e, j);
+    }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool f64 = p->prec == MG_FP64;
+  // device tables: offsets, then boundaries in the state's precision
+  // (binary32: the smallest binary32 >= the boundary)
+  std::vector<unsigned char> host;
+  const size_t o_up = a256((size_t)(g->E + 1) * 4);
+  const size_t tbytes = o_up + (size_t)nb * (f64 ? 8 : 4) + 16;
+  host.assign(tbytes, 0);
+  memcpy(host.data(), bin_offsets, (size_t)(g->E + 1) * 4);
+  for (int32_t j = 0; j < nb; ++j) {
+    if (f64) {
+      memcpy(host.data() + o_up + 8 * (size_t)j, &bin_upper[j], 8);
+    } else {
+      float f = (float)bin_upper[j];
+      if ((double)f < bin_upper[j]) f = std::nextafter(f, INFINITY);
+      memcpy(host.data() + o_up + 4 * (size_t)j, &f, 4);
+    }
+  }
+  const size_t obytes = (size_t)(nb > 0 ? nb : 1) * 4;
+  const size_t need = a256(tbytes) + (out_on_device ? 0 : a256(obytes));
+  if (p->bins_tmp.bytes < need) {
+    dev_free(p->bins_tmp, st);
+    mg_status s = dev_alloc(p->bins_tmp, need, st);
+    if (s != MG_OK) return s;
+  }
+  unsigned char* base = static_cast<unsigned char*>(p->bins_tmp.p);
+  uint32_t* dst = out_on_device ? out : reinterpret_cast<uint32_t*>(base + a256(tbytes));
+  MG_CUDA(cudaMemcpyAsync(base, host.data(), tbytes, cudaMemcpyHostToDevice, st));
+  if (nb > 0) {
+    MG_CUDA(cudaMemsetAsync(dst, 0, (size_t)nb * 4, st));
+    cudaError_t ce = mg::launch_histogram_binned(f64, p->sv.edge, p->sv.x, p->n,
+                                                 reinterpret_cast<const int32_t*>(base),
+                                                 base + o_up, nb, dst, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "mg_histogram_binned: launch");
+  }
+  p->last_stream = st;
+  if (!out_on_device) {
+    if (nb > 0) MG_CUDA(cudaMemcpyAsync(out, dst, (size_t)nb * 4, cudaMemcpyDeviceToHost, st));
+  }
+  // the host table must outlive the upload
+  MG_CUDA(cudaStreamSynchronize(st));
   return MG_OK;
 }
 

@@ -784,33 +784,4 @@ __global__ void __launch_bounds__(256) em_batch_kernel(const SimArgs* __restrict
   }
 }
 
-// Snapshot histogram of the living particles (no stepping).
-template <typename R>
-__global__ void __launch_bounds__(256) histogram_kernel(GraphView g, const int32_t* __restrict__ edge,
-                                                        const void* __restrict__ xv, int64_t n,
-                                                        int32_t bins, uint32_t* __restrict__ out,
-                                                        int32_t use_smem) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
-  const int32_t len = g.E * bins;
-  if (use_smem) {
-    block_zero(sh, len);
-    __syncthreads();
-  }
-  const R* x = reinterpret_cast<const R*>(xv);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t e = edge[i];
-    if (e < 0 || e >= g.E) continue;
-    const int32_t key = e * bins + hist_bin<R>(x[i], g.range[e], bins);
-    if (use_smem) atomicAdd(&sh[key], 1u);
-    else atomicAdd(&out[key], 1u);
-  }
-  if (use_smem) {
-    __syncthreads();
-    for (int32_t k = threadIdx.x; k < len; k += blockDim.x)
-      if (sh[k]) atomicAdd(&out[k], sh[k]);
-  }
-}
-
 }  // namespace mg

@@ -39,6 +39,13 @@ cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const 
 cudaError_t launch_histogram_f64(const GraphView& g, const int32_t* edge, const void* x, int64_t n,
                                  int32_t bins, uint32_t* out, bool smem, cudaStream_t st);
 
+// Snapshot histogram with variable-width bins (adds into out[n_bins]): off
+// [E+1] and the upper boundaries up (binary32 for binary32 states, binary64
+// otherwise) on the device.
+cudaError_t launch_histogram_binned(bool f64, const int32_t* edge, const void* x, int64_t n,
+                                    const int32_t* off, const void* up, int32_t n_bins,
+                                    uint32_t* out, cudaStream_t st);
+
 // Initialise a particle state from binary64 positions x0 (device) and edges
 // edge0 (device): copies the edges, converts x to the state's precision,
 // zeroes n_draw / hits / first_hits / flags, and sets kErrBadEdge / kErrNan in

@@ -218,6 +218,69 @@ def test_split_batching_does_not_change_results(B, prec):
         assert np.array_equal(outs[0][1]["exits"], cn["exits"])
 
 
+@pytest.mark.parametrize("prec", list(MODES))
+def test_binned_histogram_matches_oracle_rule(B, oracle, prec):
+    """Variable-width bins: the GPU's counts equal the oracle's rule applied
+    to the GPU's own final state, bit for bit, in every precision -- with
+    boundaries placed exactly on particle positions and one binary64 ulp on
+    either side of them (the binary32 boundaries are rounded up so that the
+    binary32 comparison decides as the binary64 one), edges without bins and
+    dead particles included."""
+    O = oracle
+    d = W.random_mixed(7)
+    E = len(d["src"])
+    e, x = W.uniform_on_edges(d, 30_000, 6)
+    g = B.Graph(d)
+    p = B.Particles(g, e, x, seed=2, precision=MODES[prec])
+    p.simulate(2e-3, 100, 8)
+    st = p.state()
+    es, xs = st["edge"], st["x"]
+    rng = np.random.Generator(np.random.PCG64(1))
+    off, up = [0], []
+    for k in range(E):
+        if k % 4 == 3:
+            off.append(off[-1])
+            continue
+        L = d["length"][k] if np.isfinite(d["length"][k]) else 4.0
+        b = list(rng.uniform(0.0, L, int(rng.integers(1, 10))))
+        on = xs[es == k][:3]
+        for v in on:
+            b += [v, np.nextafter(v, np.inf), np.nextafter(v, -np.inf)]
+        b = np.unique(np.array([v for v in b if v > 0.0]))
+        up += list(b)
+        off.append(off[-1] + len(b))
+    off = np.array(off, np.int32)
+    up = np.array(up)
+    h = p.histogram_binned(off, up)
+    ref = O.histogram_binned(O.Graph.from_desc(d), O.State(es, xs), off, up)
+    assert np.array_equal(h.astype(np.uint64), ref)
+    assert ref.sum() > 0 and np.count_nonzero(es < 0) > 0
+    import torch
+    hd = torch.zeros(int(off[-1]), dtype=torch.int32, device="cuda")
+    p.histogram_binned(off, up, hd)
+    assert np.array_equal(hd.cpu().numpy().astype(np.uint64), ref)
+    p.close()
+    g.close()
+
+
+def test_binned_histogram_validation(B):
+    d = W.star_brownian(3)
+    e, x = W.uniform_on_edges(d, 1000, 1)
+    g = B.Graph(d)
+    p = B.Particles(g, e, x, seed=1, precision=B.MG_FP32_MIXED)
+    for off, up in (([1, 2, 3, 4], [0.5, 0.5, 0.5, 0.5]),       # offsets[0] != 0
+                    ([0, 2, 1, 3], [0.5, 1.0, 0.5]),             # decreasing offsets
+                    ([0, 2, 2, 2], [0.5, 0.5]),                  # not increasing
+                    ([0, 1, 1, 1], [0.0]),                       # not > 0
+                    ([0, 1, 1, 1], [np.inf])):                   # not finite
+        with pytest.raises(B.MGError):
+            p.histogram_binned(np.array(off, np.int32), np.array(up, float))
+    h = p.histogram_binned(np.array([0, 0, 0, 0], np.int32), np.zeros(0))
+    assert h.sum() == 0
+    p.close()
+    g.close()
+
+
 def test_fused_histogram_matches_standalone(B):
     import torch
     d = W.star_langevin(16)
