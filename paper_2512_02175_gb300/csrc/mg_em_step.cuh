@@ -694,12 +694,16 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
       }
     }
     // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
-    // lane that went pending with an empty buffer needs up to three refills)
+    // lane that went pending with an empty buffer needs up to three refills);
+    // the count is taken once, as (kSub + 4 - held) / 4 blocks of four
     constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
+    const uint32_t held = p.n_gen - p.n_draw;
+    const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
+    if (n_ref > 0u) refill<kMode>(p, ring, a, keys, pid);
+    if (n_ref > 1u) refill<kMode>(p, ring, a, keys, pid);
 #pragma unroll
-    for (int f = 0; f < (int)(kSub + 4) / 4; ++f)
-      if (p.active && !p.pending && p.n_gen - p.n_draw <= kSub)
-        refill<kMode>(p, ring, a, keys, pid);
+    for (uint32_t f = 2; f < (kSub + 4u) / 4u; ++f)
+      if (n_ref > f) refill<kMode>(p, ring, a, keys, pid);
     if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
     const bool run = p.active && !p.pending && !p.at_v;
     if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
