@@ -190,23 +190,29 @@ def run_reference(args):
 
 # --------------------------------------------------------------- our path
 
-def _traffic(kernel_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else null)."""
+PROFILE_KEYS = ("kernel-sha256", "dram-bytes-per-launch-full-size", "issue-active-pct",
+                "warp-inst-per-warp-step")
+
+
+def _profile(kernel_hash):
+    """Figures of the committed ncu summary of the fused kernel, if it was
+    taken on the current kernel source (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", "em_step_star16_langevin.md")
     rec = {}
     try:
         with open(path) as f:
             for line in f:
-                if ":" in line and line.split(":", 1)[0] in ("kernel-sha256",
-                                                            "dram-bytes-per-launch-full-size"):
+                if ":" in line and line.split(":", 1)[0] in PROFILE_KEYS:
                     k, v = line.split(":", 1)
                     rec[k] = v.strip()
     except OSError:
-        return None
-    if rec.get("kernel-sha256") != kernel_hash:
-        return None
-    v = rec.get("dram-bytes-per-launch-full-size")
+        return {}
+    return rec if rec.get("kernel-sha256") == kernel_hash else {}
+
+
+def _traffic(kernel_hash):
+    """DRAM bytes per launch from the committed ncu summary, or null."""
+    v = _profile(kernel_hash).get("dram-bytes-per-launch-full-size")
     return int(v) if v else None
 
 
@@ -295,11 +301,15 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    prof = _profile(kernel_hash())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
                 "frac": achieved / peak, "traffic": _traffic(kernel_hash()),
                 "note": f"{I_ALG} algorithmic thread-instructions per particle-step (fast path) x "
                         f"particle-steps per launch / mean launch time; peak = "
                         f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"}
+    if prof:  # the issue-rate view, from the committed ncu capture of this kernel
+        roofline["issue_active_frac"] = float(prof["issue-active-pct"]) / 100.0
+        roofline["warp_inst_per_warp_step"] = float(prof["warp-inst-per-warp-step"])
 
     # ---- end to end through the C ABI with host buffers
     e2e = None

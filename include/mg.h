@@ -164,8 +164,15 @@ mg_status mg_particles_destroy(mg_particles p);
 /* Launch tuning of a set (the results do not depend on it): split_batch =
  * pending vertex hits in a warp that trigger a batched split pass (1..32; 0:
  * the library's default for the precision), steps_per_launch = largest number
- * of EM-Steps per kernel launch (0: no limit beyond the library's own). */
-mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t steps_per_launch);
+ * of EM-Steps per kernel launch (0: no limit beyond the library's own),
+ * max_blocks = for graphs with absorbing vertices, the most blocks of 256
+ * threads a launch uses: a set larger than that is spread evenly over the
+ * blocks, whose lanes take the next particle when theirs dies or finishes
+ * (0: the library's choice -- the blocks resident on the GPU at once, for
+ * launches of at least 1024 EM-Steps, where enough particles die for it to
+ * pay). */
+mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t steps_per_launch,
+                                  int32_t max_blocks);
 
 /* Advances every particle by `steps` EM-Steps of length dt (Algorithm 2 of
  * the paper, with sub-steps from a vertex taken into the edge with |W| as in

@@ -100,7 +100,7 @@ def _declare(L):
         "mg_particles_init": ([vp, i64, vp, vp, C.c_int, u32, u64, u32, C.c_int, vp, C.POINTER(vp)], st),
         "mg_particles_reset": ([vp, vp, vp, C.c_int, vp], st),
         "mg_particles_destroy": ([vp], st),
-        "mg_particles_set_tuning": ([vp, i32, i64], st),
+        "mg_particles_set_tuning": ([vp, i32, i64, i32], st),
         "mg_simulate": ([vp, dbl, i64, i32, i32, vp, vp], st),
         "mg_simulate_sampled": ([vp, dbl, i64, i32, i64, i32, vp, vp], st),
         "mg_histogram_binned": ([vp, vp, vp, vp, C.c_int, vp], st),
@@ -273,8 +273,9 @@ def mg_particles_destroy(p):
     _check(load().mg_particles_destroy(p))
 
 
-def mg_particles_set_tuning(p, split_batch=0, steps_per_launch=0):
-    _check(load().mg_particles_set_tuning(p, int(split_batch), int(steps_per_launch)))
+def mg_particles_set_tuning(p, split_batch=0, steps_per_launch=0, max_blocks=0):
+    _check(load().mg_particles_set_tuning(p, int(split_batch), int(steps_per_launch),
+                                          int(max_blocks)))
 
 
 def mg_particles_info(p):
@@ -487,8 +488,8 @@ class Particles:
         self.h = mg_particles_init(graph.h, edge0, x0, pid_base=pid_base, seed=seed,
                                    instance=instance, precision=precision, stream=stream)
 
-    def set_tuning(self, split_batch=0, steps_per_launch=0):
-        mg_particles_set_tuning(self.h, split_batch, steps_per_launch)
+    def set_tuning(self, split_batch=0, steps_per_launch=0, max_blocks=0):
+        mg_particles_set_tuning(self.h, split_batch, steps_per_launch, max_blocks)
 
     def simulate(self, dt, steps, M, hist_bins=0, hist_out=None, stream=None):
         mg_simulate(self.h, dt, steps, M, hist_bins, hist_out, stream)

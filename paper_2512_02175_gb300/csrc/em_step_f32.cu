@@ -13,6 +13,8 @@ static void set_smem_attributes() {
   if (!done) {
     cudaFuncSetAttribute(em_step_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute(em_range_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaFuncSetAttribute(em_batch_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     done = true;
@@ -21,15 +23,35 @@ static void set_smem_attributes() {
 
 cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
                                 cudaStream_t st) {
-  const int64_t grid = (a.n + kBlock - 1) / kBlock;
+  const int64_t grid = (a.n + a.range - 1) / a.range;
+  const bool ranged = a.range > kBlock;
   if (mode == kModeMixed) {
     set_smem_attributes<kModeMixed>();
-    em_step_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+    if (ranged) em_range_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+    else em_step_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
   } else {
     set_smem_attributes<kModeF32>();
-    em_step_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+    if (ranged) em_range_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+    else em_step_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
   }
   return cudaGetLastError();
+}
+
+int em_range_blocks_per_sm_f32x(int mode, size_t smem) {
+  int nb = 0;
+  if (mode == kModeMixed) {
+    set_smem_attributes<kModeMixed>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeMixed>, kBlock, smem);
+  } else {
+    set_smem_attributes<kModeF32>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeF32>, kBlock, smem);
+  }
+  return nb;
+}
+
+int em_range_blocks_per_sm(int mode, size_t smem) {
+  return mode == kModeF64 ? em_range_blocks_per_sm_f64(smem)
+                          : em_range_blocks_per_sm_f32x(mode, smem);
 }
 
 cudaError_t launch_em_batch_f32x(int mode, const SimArgs* insts, const BatchItem* items,

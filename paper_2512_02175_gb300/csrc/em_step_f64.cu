@@ -13,6 +13,8 @@ static void set_smem_attributes() {
   if (!done) {
     cudaFuncSetAttribute(em_step_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute(em_range_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaFuncSetAttribute(em_batch_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     done = true;
@@ -21,9 +23,17 @@ static void set_smem_attributes() {
 
 cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cudaStream_t st) {
   set_smem_attributes();
-  const int64_t grid = (a.n + kBlock - 1) / kBlock;
-  em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+  const int64_t grid = (a.n + a.range - 1) / a.range;
+  if (a.range > kBlock) em_range_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+  else em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
   return cudaGetLastError();
+}
+
+int em_range_blocks_per_sm_f64(size_t smem) {
+  set_smem_attributes();
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeF64>, kBlock, smem);
+  return nb;
 }
 
 cudaError_t launch_em_batch_f64(const SimArgs* insts, const BatchItem* items, int32_t n_items,

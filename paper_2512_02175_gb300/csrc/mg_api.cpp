@@ -100,6 +100,7 @@ struct mg_graph_s {
   // host copies
   std::vector<int32_t> src, dst, vtx_off, slot_edge, slot_of_end;
   std::vector<uint8_t> slot_end, kind;
+  bool has_absorbing = false;  // particles can die
   std::vector<uint64_t> slot_T;
   std::vector<double> length, range;
   // device tables (one allocation)
@@ -170,6 +171,8 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
     g->range[e] = d->hist_range ? d->hist_range[e] : (g->dst[e] >= 0 ? g->length[e] : 1.0);
   g->kind.assign(V, 0);
   if (d->vertex_kind) g->kind.assign(d->vertex_kind, d->vertex_kind + V);
+  for (int32_t v = 0; v < V; ++v)
+    if (g->kind[v] == MG_VERTEX_ABSORBING) g->has_absorbing = true;
 
   // Slots by counting sort on the vertex: each edge contributes its init end
   // then its term end, edges in id order, so within a vertex the slots are
@@ -338,6 +341,7 @@ struct mg_particles_s {
   uint64_t step = 0;
   int32_t split_batch = 0;       // 0: the library's default for the mode
   int64_t steps_per_launch = 0;  // 0: as many as fit one launch
+  int32_t max_blocks = 0;        // range kernel: most blocks per launch (0: resident)
   DevBuf state;      // edge | x | n_draw | hits | first_hits | flags
   DevBuf counters;   // exits[S] | absorbed[V] | trunc | psteps | err
   DevBuf hist_tmp;   // histogram staging for host output
@@ -504,13 +508,15 @@ constexpr size_t kSmemBudget = 24 * 1024;
 }  // namespace
 
 extern "C" mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch,
-                                             int64_t steps_per_launch) {
+                                             int64_t steps_per_launch, int32_t max_blocks) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_particles_set_tuning: NULL particles");
   if (split_batch < 0 || split_batch > 32)
     return fail(MG_ERR_INVALID_ARG, "split_batch must be in [0, 32]");
   if (steps_per_launch < 0) return fail(MG_ERR_INVALID_ARG, "steps_per_launch must be >= 0");
+  if (max_blocks < 0) return fail(MG_ERR_INVALID_ARG, "max_blocks must be >= 0");
   p->split_batch = split_batch;
   p->steps_per_launch = steps_per_launch;
+  p->max_blocks = max_blocks;
   return MG_OK;
 }
 
@@ -565,6 +571,7 @@ Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32
   a.s = p->sv;
   a.c = p->cv;
   a.n = p->n;
+  a.range = mg::kBlock;
   a.pid_base = p->pid_base;
   a.instance = p->instance;
   a.dt = dt;
@@ -592,9 +599,10 @@ Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32
   return pl;
 }
 
-// Most EM-Steps one launch may take: 2^31 - 1 (the per-lane step counter);
-// with 32-bit shared counters 2^32 / (256 (2M + 1)) so they cannot wrap; and
-// the kernel's loop guard, 32 steps (2M + 2) + 64, must fit 32 bits.
+// Most EM-Steps one launch may take: the kernel's loop guard, 32 steps
+// (2M + 2) + 64, must fit 32 bits (and so does the per-lane step counter);
+// with 32-bit shared counters in blocks of 256 particles, 2^32 / (256 (2M + 1))
+// so that they cannot wrap.
 int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
   int64_t chunk = (int64_t)((4294967295ull - 64ull) / (32ull * (2ull * (uint64_t)M + 2ull)));
   if (smem_counters) {
@@ -602,6 +610,32 @@ int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
     if (chunk > cap) chunk = cap;
   }
   return chunk < 1 ? 1 : chunk;
+}
+
+// Particles per block of mg_simulate: 256 (one per thread, em_step_kernel),
+// unless particles can die, the set is larger than the blocks resident at
+// once (or max_blocks) and a launch is long enough for many of them to die:
+// then the set is spread evenly over those blocks and em_range_kernel's lanes
+// claim the next particle when theirs dies or finishes.  Its larger register
+// footprint (four blocks per SM instead of five) costs ~15%, repaid once most
+// particles die within the launch: on the synthetic vascular network the two
+// kernels break even near 1000 EM-Steps per launch (65% absorbed) and the
+// range kernel is 15% faster at 2000 (81%).  An explicit max_blocks selects it
+// for any launch length.
+constexpr int64_t kRangeMinSteps = 1024;
+
+int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
+  const int64_t tiles = (p->n + mg::kBlock - 1) / mg::kBlock;
+  if (!p->g->has_absorbing) return mg::kBlock;
+  if (p->max_blocks == 0 && steps_per_launch < kRangeMinSteps) return mg::kBlock;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = mg::em_range_blocks_per_sm((int)p->prec, smem);
+  int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  if (p->max_blocks > 0 && p->max_blocks < blocks) blocks = p->max_blocks;
+  if (tiles <= blocks) return mg::kBlock;
+  return (p->n + blocks - 1) / blocks;
 }
 
 mg_status check_step_args(double dt, int64_t steps, int32_t M, int32_t hist_bins,
@@ -626,6 +660,13 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   const mg_graph g = p->g;
   Plan pl = plan_launch(p, dt, M, hist_bins, hist_out, (size_t)-1, p->split_batch);
   const mg::Keys keys = keys_of(p->seed);
+  int64_t first = std::min(steps, max_steps_per_launch(M, false));
+  if (p->steps_per_launch > 0) first = std::min(first, p->steps_per_launch);
+  pl.a.range = block_range(p, pl.smem(true, g), first);
+  if (pl.a.range > mg::kBlock) {  // blocks run many particles: 64-bit global counters
+    pl.counters = false;
+    pl.a.smem_counters = 0;
+  }
   int64_t chunk = max_steps_per_launch(M, pl.counters);
   if (p->steps_per_launch > 0 && p->steps_per_launch < chunk) chunk = p->steps_per_launch;
   int64_t done = 0;

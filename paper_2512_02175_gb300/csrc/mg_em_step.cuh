@@ -187,6 +187,10 @@ __device__ __forceinline__ int32_t choose_slot(const GraphView& g, const VtxRec&
   return j;
 }
 
+// Exit and absorption counters of a block, privatised in shared memory when
+// they fit (32-bit: a tile of 256 particles cannot overflow them within one
+// launch; the range kernel, whose blocks run many particles, counts in
+// global memory).
 struct BlockCounters {
   uint32_t* exits;     // shared [S] or nullptr (then global atomics)
   uint32_t* absorbed;  // shared [V] or nullptr
@@ -576,6 +580,114 @@ __device__ __forceinline__ void block_zero(T* dst, int32_t n) {
 
 // ------------------------------------------------------------- the kernel
 
+// A block's view of its working set: graph tables (staged in shared memory
+// when they fit), privatised counters and histogram, the normal ring.
+template <int kMode>
+struct BlockSetup {
+  GraphView g;
+  BlockCounters bc;
+  uint32_t* shist;
+  int32_t hist_len;
+  typename Types<kMode>::R* ring;
+};
+
+// Stages the tables and zeroes the privatised counters (the caller
+// synchronises the block before use).
+template <int kMode>
+__device__ __forceinline__ BlockSetup<kMode> setup_block(const SimArgs& a, unsigned char* smem) {
+  using R = typename Types<kMode>::R;
+  constexpr bool kF64 = kMode == kModeF64;
+  BlockSetup<kMode> b;
+  b.g = a.g;
+  GraphView& g = b.g;
+  b.hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
+  const SmemLayout lay = smem_layout(g.V, g.E, g.S, g.G, kF64, a.stage_smem, a.smem_counters,
+                                     b.hist_len, kThreads);
+  if (a.stage_smem) {
+    if constexpr (kF64) {
+      block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
+      g.e64 = reinterpret_cast<const EdgeRec64*>(smem + lay.edges);
+    } else {
+      block_copy(reinterpret_cast<EdgeRec32*>(smem + lay.edges), g.e32, g.E);
+      g.e32 = reinterpret_cast<const EdgeRec32*>(smem + lay.edges);
+    }
+    block_copy(reinterpret_cast<SlotRec*>(smem + lay.slots), g.slot, g.S);
+    block_copy(reinterpret_cast<VtxRec*>(smem + lay.vtx), g.vtx, g.V);
+    block_copy(reinterpret_cast<int32_t*>(smem + lay.guide), g.guide, g.G);
+    g.slot = reinterpret_cast<const SlotRec*>(smem + lay.slots);
+    g.vtx = reinterpret_cast<const VtxRec*>(smem + lay.vtx);
+    g.guide = reinterpret_cast<const int32_t*>(smem + lay.guide);
+  }
+  b.bc = BlockCounters{nullptr, nullptr};
+  if (a.smem_counters) {
+    b.bc.exits = reinterpret_cast<uint32_t*>(smem + lay.exits);
+    b.bc.absorbed = reinterpret_cast<uint32_t*>(smem + lay.absorbed);
+    block_zero(b.bc.exits, g.S);
+    block_zero(b.bc.absorbed, g.V);
+  }
+  b.shist = a.smem_hist ? reinterpret_cast<uint32_t*>(smem + lay.hist) : nullptr;
+  if (b.shist) block_zero(b.shist, b.hist_len);
+  b.ring = reinterpret_cast<R*>(smem + lay.ring);
+  return b;
+}
+
+// Adds the block's privatised counters and histogram to the global ones
+// (after the block's last use of them).
+template <int kMode>
+__device__ __forceinline__ void flush_block(const SimArgs& a, const BlockSetup<kMode>& b) {
+  __syncthreads();
+  if (a.smem_counters) {
+    for (int32_t k = threadIdx.x; k < b.g.S; k += blockDim.x)
+      if (b.bc.exits[k]) atomicAdd(&a.c.exits[k], (unsigned long long)b.bc.exits[k]);
+    for (int32_t k = threadIdx.x; k < b.g.V; k += blockDim.x)
+      if (b.bc.absorbed[k]) atomicAdd(&a.c.absorbed[k], (unsigned long long)b.bc.absorbed[k]);
+  }
+  if (b.shist)
+    for (int32_t k = threadIdx.x; k < b.hist_len; k += blockDim.x)
+      if (b.shist[k]) atomicAdd(&a.hist[k], b.shist[k]);
+}
+
+// One iteration of a warp after its liveness check: the split pass (each
+// pending lane's whole chain of vertex hits), the refills, the sub-step from
+// a vertex, and kSub interior sub-steps.
+template <int kMode>
+__device__ __forceinline__ void iteration(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
+                                          const Keys& keys, const BlockCounters& bc,
+                                          typename Types<kMode>::R* ring, uint32_t pid,
+                                          uint32_t& trunc, uint32_t am) {
+  const uint32_t full = 0xffffffffu;
+  const uint32_t pm = __ballot_sync(full, p.pending);
+  if (pm != 0u && (__popc(pm) >= a.split_batch || pm == am)) {
+    // resolve each pending lane's whole chain of vertex hits in this pass:
+    // split, then the sub-step from the vertex, which may hit again (at
+    // most M times: the M-th split ends the step)
+    while (p.pending) {
+      split<kMode>(p, g, a, keys, bc, ring, pid, trunc);
+      if (!p.active || !p.in_cont) break;
+      if (p.n_gen == p.n_draw) {  // the chain has used up the buffer
+        refill<kMode>(p, ring, a, keys, pid);
+        if (!p.active) break;
+      }
+      vertex_sub_step<kMode>(p, ring, a, bc);
+    }
+  }
+  // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
+  // lane that went pending with an empty buffer needs up to three refills);
+  // the count is taken once, as (kSub + 4 - held) / 4 blocks of four
+  constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
+  const uint32_t held = p.n_gen - p.n_draw;
+  const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
+  if (n_ref > 0u) refill<kMode>(p, ring, a, keys, pid);
+  if (n_ref > 1u) refill<kMode>(p, ring, a, keys, pid);
+#pragma unroll
+  for (uint32_t f = 2; f < (kSub + 4u) / 4u; ++f)
+    if (n_ref > f) refill<kMode>(p, ring, a, keys, pid);
+  if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
+  const bool run = p.active && !p.pending && !p.at_v;
+  if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
+  else interior_quad<kMode, true>(p, ring, run);
+}
+
 // One block's tile of a particle set: particle i of the calling thread
 // (i >= a.n: an idle lane that still takes part in the block's barriers).
 template <int kMode>
@@ -750,6 +862,189 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
   if (shist)
     for (int32_t k = threadIdx.x; k < hist_len; k += blockDim.x)
       if (shist[k]) atomicAdd(&a.hist[k], shist[k]);
+}
+
+// A block's claim on its range of particles (range kernel), in shared
+// memory: the next unclaimed index, the end of the range, and the block's
+// totals of steps taken while alive and of truncated steps.
+struct RangeCtl {
+  unsigned long long next;
+  long long hi;
+  unsigned long long psteps, trunc;
+};
+
+// Loads particle i into the lane (state, edge, whole-step coefficients and
+// the first four normals of its stream) and returns whether it moves: alive,
+// valid and with steps to take.  A particle that does not move is written
+// back at once (if valid: unchanged, plus its histogram bin); an invalid edge
+// or position sets the device-error bit and leaves it untouched.
+template <int kMode>
+__device__ __forceinline__ bool load_particle(Lane<kMode>& p, uint32_t& pid, const SimArgs& a,
+                                              const Keys& keys, const GraphView& g,
+                                              typename Types<kMode>::R* ring, uint32_t* shist,
+                                              int64_t i) {
+  using R = typename Types<kMode>::R;
+  pid = a.pid_base + (uint32_t)i;
+  p.active = false;
+  p.pending = false;
+  p.e = a.s.edge[i];
+  p.x = reinterpret_cast<const R*>(a.s.x)[i];
+  p.n_draw = a.s.n_draw[i];
+  p.hits = a.s.hits[i];
+  p.first_hits = a.s.first_hits[i];
+  p.flags = a.s.flags[i];
+  bool ok = p.e >= kDead && p.e < g.E;
+  if (!ok) atomicOr(a.c.err, kErrBadEdge);
+  if (ok && p.e >= 0) {
+    const R x0 = p.x;
+    enter_edge<kMode>(p, g, p.e, a);
+    p.x = x0;
+    if (!(p.x >= R(0) && p.x <= p.L)) {
+      atomicOr(a.c.err, kErrNan);
+      ok = false;
+    }
+  }
+  if (!ok) return false;
+  if (p.e < 0 || a.steps <= 0) {  // dead, or nothing to do: only the histogram
+    if (a.hist_bins > 0 && p.e >= 0) {
+      const int32_t key = p.e * a.hist_bins + hist_bin<R>(p.x, g.range[p.e], a.hist_bins);
+      if (shist) atomicAdd(&shist[key], 1u);
+      else atomicAdd(&a.hist[key], 1u);
+    }
+    return false;
+  }
+  p.active = true;
+  p.left = (uint32_t)a.steps;
+  p.k = 0;
+  p.in_cont = false;
+  use_step_coefficients(p, a);
+  p.at_v = (p.x == R(0)) || (p.x == p.L);
+  p.wand = 0xffffffffu;
+  p.wor = 0u;
+  p.cur_slot = -1;
+  if (p.at_v) {
+    const int32_t end = (p.x == R(0)) ? kEndInit : kEndTerm;
+    if constexpr (kMode == kModeF64)
+      p.cur_slot = (end == kEndInit) ? g.e64[p.e].slot_init : g.e64[p.e].slot_term;
+    else
+      p.cur_slot = (end == kEndInit) ? g.e32[p.e].slot_init : g.e32[p.e].slot_term;
+    set_vertex_sign(p, end);
+  }
+  p.n_gen = p.n_draw & ~3u;
+  refill<kMode>(p, ring, a, keys, pid);
+  return true;
+}
+
+// Writes back a particle that moved in this launch: state, steps taken while
+// alive (an absorbed particle took the step it died in), its truncations and
+// its bin of the fused snapshot histogram.
+template <int kMode>
+__device__ __forceinline__ void finish_particle(const Lane<kMode>& p, uint32_t pid,
+                                                uint32_t& trunc, const SimArgs& a,
+                                                const GraphView& g, uint32_t* shist,
+                                                RangeCtl* ctl) {
+  using R = typename Types<kMode>::R;
+  const int64_t i = (int64_t)(uint32_t)(pid - a.pid_base);
+  atomicAdd(&ctl->psteps,
+            (unsigned long long)((uint64_t)a.steps - p.left + ((p.e < 0) ? 1u : 0u)));
+  if (trunc) atomicAdd(&ctl->trunc, (unsigned long long)trunc);
+  trunc = 0;
+  a.s.edge[i] = p.e;
+  reinterpret_cast<R*>(a.s.x)[i] = p.x;
+  a.s.n_draw[i] = p.n_draw;
+  a.s.hits[i] = p.hits;
+  a.s.first_hits[i] = p.first_hits;
+  a.s.flags[i] = p.flags;
+  if (a.hist_bins > 0 && p.e >= 0) {
+    const int32_t key = p.e * a.hist_bins + hist_bin<R>(p.x, g.range[p.e], a.hist_bins);
+    if (shist) atomicAdd(&shist[key], 1u);
+    else atomicAdd(&a.hist[key], 1u);
+  }
+}
+
+// One block's range [lo, hi) of a particle set, for sets whose particles can
+// die (absorbing vertices): thread t starts with particle lo + t, and a lane
+// whose particle has taken all its steps or died writes it back and claims
+// the next particle of the range, so lanes stay busy until the range runs out
+// instead of idling beside their warp's last survivor.  A particle's result
+// does not depend on the lane, block or order that runs it.
+template <int kMode>
+__device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, int64_t lo,
+                                          int64_t hi, unsigned char* smem, RangeCtl* ctl) {
+  const BlockSetup<kMode> blk = setup_block<kMode>(a, smem);  // a.smem_counters == 0
+  const GraphView& g = blk.g;
+  if (threadIdx.x == 0) {
+    ctl->next = (unsigned long long)(lo + blockDim.x);
+    ctl->hi = hi;
+    ctl->psteps = 0;
+    ctl->trunc = 0;
+  }
+  __syncthreads();
+
+  uint32_t trunc = 0;  // truncated steps of the lane's current particle
+  uint32_t pid = 0;    // global id of the lane's particle
+  Lane<kMode> p;
+  p.active = false;
+  p.pending = false;
+  bool held = false;   // the lane holds a moving particle (to be written back)
+  bool claim = true;   // the block's range may still have particles for it
+  if (lo + (int64_t)threadIdx.x < hi)
+    held = load_particle<kMode>(p, pid, a, keys, g, blk.ring, blk.shist,
+                                lo + (int64_t)threadIdx.x);
+
+  // As in run_tile, plus: between two iterations in which a lane of the warp
+  // takes a new particle, every iteration moves one of the at most 32
+  // particles held by a sub-step or a split, so `quads`, restarted whenever a
+  // lane takes a particle, stays within 32 steps (2M + 2) + 64.
+  const uint32_t full = 0xffffffffu;
+  const uint32_t cap = 32u * (uint32_t)a.steps * (uint32_t)(2 * a.M + 2) + 64u;
+  uint32_t quads = 0;
+  for (;;) {
+    bool took = false;
+    if (!p.active && claim) {
+      // write back the finished particle, then claim the next one that moves
+      if (held) finish_particle<kMode>(p, pid, trunc, a, g, blk.shist, ctl);
+      held = false;
+      do {
+        const int64_t nx = (int64_t)atomicAdd(&ctl->next, 1ull);
+        if (nx >= ctl->hi) {
+          claim = false;
+          break;
+        }
+        took = true;
+        held = load_particle<kMode>(p, pid, a, keys, g, blk.ring, blk.shist, nx);
+      } while (!held);
+    }
+    if (__any_sync(full, took)) quads = 0;
+    const uint32_t am = __ballot_sync(full, p.active);
+    if (am == 0u) break;
+    if (++quads > cap) {
+      if (p.active) atomicOr(a.c.err, kErrStuck);
+      break;
+    }
+    iteration<kMode>(p, g, a, keys, blk.bc, blk.ring, pid, trunc, am);
+  }
+  // after the last particle, or a loop left through the cap: write back what
+  // the lane holds
+  if (held) finish_particle<kMode>(p, pid, trunc, a, g, blk.shist, ctl);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (ctl->trunc) atomicAdd(a.c.trunc, ctl->trunc);
+    if (ctl->psteps) atomicAdd(a.c.psteps, ctl->psteps);
+  }
+  flush_block<kMode>(a, blk);
+}
+
+// The range form of the fused EM-Step kernel: block b runs particles
+// [b range, (b + 1) range) of one set with lanes that claim particles.
+template <int kMode>
+__global__ void __launch_bounds__(256) em_range_kernel(const __grid_constant__ SimArgs a,
+                                                       const __grid_constant__ Keys keys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ RangeCtl ctl;
+  const int64_t lo = (int64_t)blockIdx.x * a.range;
+  const int64_t hi = (lo + a.range < a.n) ? lo + a.range : a.n;
+  run_range<kMode>(a, keys, lo, hi, smem, &ctl);
 }
 
 // The fused EM-Step kernel over one particle set: block b takes particles

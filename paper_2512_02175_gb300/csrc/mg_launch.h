@@ -15,6 +15,12 @@ cudaError_t launch_em_step(int mode, const SimArgs& a, const Keys& k, size_t sme
 cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cudaStream_t st);
 cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
                                 cudaStream_t st);
+// (a.range > 256 launches the range kernel: lanes claim particles of their
+// block's range.)  Resident blocks per SM of the range kernel at `smem` bytes
+// of dynamic shared memory.
+int em_range_blocks_per_sm(int mode, size_t smem);
+int em_range_blocks_per_sm_f64(size_t smem);
+int em_range_blocks_per_sm_f32x(int mode, size_t smem);
 
 // The batched persistent kernel: `blocks` blocks pop the n_items work items
 // (head must be zero at launch).  blocks_per_sm: resident blocks per SM at

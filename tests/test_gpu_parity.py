@@ -281,6 +281,39 @@ def test_binned_histogram_validation(B):
     g.close()
 
 
+@pytest.mark.parametrize("prec", list(MODES))
+def test_particles_per_block_do_not_change_results(B, prec):
+    """A graph with absorbing vertices runs a set larger than the resident
+    blocks with lanes that take the next particle when theirs dies or
+    finishes: bit for bit the same results as one particle per thread (here
+    forced with few blocks), including particles already dead at the second
+    launch, split batches above one and the fused histogram."""
+    import torch
+    d = W.random_mixed(7)
+    assert np.any(np.asarray(d["kind"]) == 1)
+    e, x = W.uniform_on_edges(d, 20_000, 4)
+    g = B.Graph(d)
+    outs = []
+    for blocks, sb in ((0, 1), (1, 1), (3, 5), (7, 32)):
+        p = B.Particles(g, e, x, seed=8, precision=MODES[prec])
+        p.set_tuning(split_batch=sb, max_blocks=blocks)
+        h = torch.zeros(g.n_edges * 8, dtype=torch.int32, device="cuda")
+        p.simulate(3e-3, 150, 8, hist_bins=8, hist_out=h)
+        p.simulate(3e-3, 70, 8)
+        p.synchronize()
+        outs.append((p.state(), p.counts(), h.cpu().numpy()))
+        p.close()
+    g.close()
+    ref_state, ref_counts, ref_hist = outs[0]
+    assert ref_counts["absorbed"].sum() > 0
+    for st, cn, hist in outs[1:]:
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+            assert np.array_equal(ref_state[k], st[k]), k
+        for k in ("exits", "absorbed", "truncations", "particle_steps"):
+            assert np.array_equal(np.asarray(ref_counts[k]), np.asarray(cn[k])), k
+        assert np.array_equal(ref_hist, hist)
+
+
 def test_fused_histogram_matches_standalone(B):
     import torch
     d = W.star_langevin(16)
