@@ -370,7 +370,9 @@ __device__ __forceinline__ typename Types<kMode>::R sub_step_end(const Lane<kMod
     const double b_ = p.S * W;
     return p.x + a_ + b_;
   } else {
-    return fmaf(p.S, W, fmaf(p.x, p.Q, p.P));
+    // x Q + (S W + P): the same expression (and rounding) as the interior
+    // sub-steps, so a recomputed end point falls on the same side
+    return fmaf(p.x, p.Q, fmaf(p.S, W, p.P));
   }
 }
 
@@ -422,6 +424,10 @@ __device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Typ
   const uint32_t lim = kCheckLeft ? (p.left < kSub ? p.left : kSub) : kSub;
   uint32_t n_in = 0;
   bool go = run;
+  // binary32: the end points are chained unselected (xc), so each sub-step
+  // adds one FMA on x to the dependency chain; xc equals x for every
+  // sub-step that counts
+  R xc = p.x;
 #pragma unroll
   for (int q = 0; q < (int)kSub; ++q) {
     const bool att = go && (!kCheckLeft || (uint32_t)q < lim);
@@ -434,7 +440,8 @@ __device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Typ
       xt = p.x + a_ + b_;
       if (att) mark_near_branch(p, xt);
     } else {
-      xt = fmaf(p.Sm, z, fmaf(p.x, p.Qm, p.Pm));
+      xt = fmaf(xc, p.Qm, fmaf(p.Sm, z, p.Pm));
+      xc = xt;
     }
     const bool in = att & (xt > R(0)) & (xt < p.L);
     p.x = in ? xt : p.x;
