@@ -73,6 +73,30 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
   return {c0, c1, c2, c3};
 }
 
+// Two Philox-4x32-10 blocks with counters (c0a, c1, c2, c3) and (c0b, c1, c2,
+// c3), their rounds interleaved so that the two independent multiply chains
+// overlap.
+__device__ __forceinline__ void philox4x32_10_x2(uint32_t c0a, uint32_t c0b, uint32_t c1,
+                                                 uint32_t c2, uint32_t c3,
+                                                 const uint32_t* __restrict__ rk, U4& wa,
+                                                 U4& wb) {
+  uint32_t a0 = c0a, a1 = c1, a2 = c2, a3 = c3;
+  uint32_t b0 = c0b, b1 = c1, b2 = c2, b3 = c3;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t alo0 = 0xD2511F53u * a0, ahi0 = __umulhi(0xD2511F53u, a0);
+    const uint32_t alo1 = 0xCD9E8D57u * a2, ahi1 = __umulhi(0xCD9E8D57u, a2);
+    const uint32_t blo0 = 0xD2511F53u * b0, bhi0 = __umulhi(0xD2511F53u, b0);
+    const uint32_t blo1 = 0xCD9E8D57u * b2, bhi1 = __umulhi(0xCD9E8D57u, b2);
+    const uint32_t an0 = ahi1 ^ a1 ^ rk[2 * r], an2 = ahi0 ^ a3 ^ rk[2 * r + 1];
+    const uint32_t bn0 = bhi1 ^ b1 ^ rk[2 * r], bn2 = bhi0 ^ b3 ^ rk[2 * r + 1];
+    a0 = an0; a1 = alo1; a2 = an2; a3 = alo0;
+    b0 = bn0; b1 = blo1; b2 = bn2; b3 = blo0;
+  }
+  wa = {a0, a1, a2, a3};
+  wb = {b0, b1, b2, b3};
+}
+
 // ------------------------------------------------------------- Box-Muller
 
 // binary64: u = (2w + 1) 2^-33, r = sqrt(-2 ln u_a), theta = 2 pi u_b.
@@ -358,6 +382,60 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
   r[(K + 2) * kThreads] = z2;
   r[(K + 3) * kThreads] = z3;
   p.n_gen += 4;
+}
+
+// Eight normals at once (binary32 modes): the next two Philox blocks of the
+// lane's stream, computed interleaved.  Only for a lane that holds at most
+// kSub = 8 normals, so that the ring's 16 cannot overflow.
+template <int kMode>
+__device__ __forceinline__ void refill8(Lane<kMode>& p, typename Types<kMode>::R* ring,
+                                        const SimArgs& a, const Keys& keys, uint32_t pid) {
+  static_assert(kMode != kModeF64, "binary32 modes only");
+  if (p.n_gen >= 0xFFFFFFF0u - 4u) {
+    atomicOr(a.c.err, kErrStream);
+    p.active = false;
+    p.pending = false;
+    return;
+  }
+  U4 wa, wb;
+  philox4x32_10_x2(p.n_gen >> 2, (p.n_gen >> 2) + 1u, pid, 0u, a.instance, keys.rk, wa, wb);
+  float z[8];
+  box_muller_f32(wa.x, wa.y, z[0], z[1]);
+  box_muller_f32(wa.z, wa.w, z[2], z[3]);
+  box_muller_f32(wb.x, wb.y, z[4], z[5]);
+  box_muller_f32(wb.z, wb.w, z[6], z[7]);
+  constexpr uint32_t K = Types<kMode>::kRing;
+  float* ra = ring + (p.n_gen & (K - 1u)) * kThreads + threadIdx.x;
+  float* rb = ring + ((p.n_gen + 4u) & (K - 1u)) * kThreads + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ra[k * kThreads] = z[k];
+    ra[(K + k) * kThreads] = z[k];
+    rb[k * kThreads] = z[4 + k];
+    rb[(K + k) * kThreads] = z[4 + k];
+  }
+  p.n_gen += 8;
+}
+
+// The refills of an iteration: top the buffer up to at least kSub + 1
+// normals (an iteration uses up to kSub + 1; a lane that went pending with an
+// empty buffer needs up to three blocks of four).  Binary32 modes take two
+// blocks at once whenever any are needed (the lane holds at most 8, so 16
+// fit), and a third for an empty buffer.
+template <int kMode>
+__device__ __forceinline__ void refill_iteration(Lane<kMode>& p, typename Types<kMode>::R* ring,
+                                                 const SimArgs& a, const Keys& keys,
+                                                 uint32_t pid) {
+  constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
+  const uint32_t held = p.n_gen - p.n_draw;
+  const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
+  if constexpr (kMode != kModeF64) {
+    if (n_ref > 0u) refill8<kMode>(p, ring, a, keys, pid);
+    if (n_ref > 2u) refill<kMode>(p, ring, a, keys, pid);
+  } else {
+    if (n_ref > 0u) refill<kMode>(p, ring, a, keys, pid);
+    if (n_ref > 1u) refill<kMode>(p, ring, a, keys, pid);
+  }
 }
 
 // End point of a sub-step with normal W over the lane's current time h.
@@ -678,17 +756,8 @@ __device__ __forceinline__ void iteration(Lane<kMode>& p, const GraphView& g, co
       vertex_sub_step<kMode>(p, ring, a, bc);
     }
   }
-  // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
-  // lane that went pending with an empty buffer needs up to three refills);
-  // the count is taken once, as (kSub + 4 - held) / 4 blocks of four
+  refill_iteration<kMode>(p, ring, a, keys, pid);
   constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
-  const uint32_t held = p.n_gen - p.n_draw;
-  const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
-  if (n_ref > 0u) refill<kMode>(p, ring, a, keys, pid);
-  if (n_ref > 1u) refill<kMode>(p, ring, a, keys, pid);
-#pragma unroll
-  for (uint32_t f = 2; f < (kSub + 4u) / 4u; ++f)
-    if (n_ref > f) refill<kMode>(p, ring, a, keys, pid);
   if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
   const bool run = p.active && !p.pending && !p.at_v;
   if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
@@ -812,17 +881,8 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
         vertex_sub_step<kMode>(p, ring, a, bc);
       }
     }
-    // an iteration uses up to kSub + 1 normals: top the buffer up to that (a
-    // lane that went pending with an empty buffer needs up to three refills);
-    // the count is taken once, as (kSub + 4 - held) / 4 blocks of four
+    refill_iteration<kMode>(p, ring, a, keys, pid);
     constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
-    const uint32_t held = p.n_gen - p.n_draw;
-    const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
-    if (n_ref > 0u) refill<kMode>(p, ring, a, keys, pid);
-    if (n_ref > 1u) refill<kMode>(p, ring, a, keys, pid);
-#pragma unroll
-    for (uint32_t f = 2; f < (kSub + 4u) / 4u; ++f)
-      if (n_ref > f) refill<kMode>(p, ring, a, keys, pid);
     if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
     const bool run = p.active && !p.pending && !p.at_v;
     if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
