@@ -616,13 +616,13 @@ int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
 // unless particles can die, the set is larger than the blocks resident at
 // once (or max_blocks) and a launch is long enough for many of them to die:
 // then the set is spread evenly over those blocks and em_range_kernel's lanes
-// claim the next particle when theirs dies or finishes.  Its larger register
-// footprint (four blocks per SM instead of five) costs ~15%, repaid once most
-// particles die within the launch: on the synthetic vascular network the two
-// kernels break even near 1000 EM-Steps per launch (65% absorbed) and the
-// range kernel is 15% faster at 2000 (81%).  An explicit max_blocks selects it
-// for any launch length.
-constexpr int64_t kRangeMinSteps = 1024;
+// claim the next particle when theirs dies or finishes.  Its bookkeeping
+// (claims, global counters) costs ~10% when few particles die, repaid once
+// many die within the launch: on the synthetic vascular network (2^24
+// tracers) range / tile throughput is 0.90 at 250 EM-Steps per launch (30%
+// absorbed), 0.94 at 500, 1.03 at 1000 (65%).  An explicit max_blocks selects
+// it for any launch length.
+constexpr int64_t kRangeMinSteps = 768;
 
 int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
   const int64_t tiles = (p->n + mg::kBlock - 1) / mg::kBlock;

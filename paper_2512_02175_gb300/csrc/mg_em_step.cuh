@@ -542,6 +542,9 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   p.pending = false;
+  // the jump draw of this hit (block (j, pid, 1, instance), j = hits so far),
+  // first: its chain of multiplies overlaps the hitting-fraction arithmetic
+  const U4 w = philox4x32_10(p.hits, pid, 1u, a.instance, keys.rk);
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
   const R Wp = apply_sign(
@@ -602,7 +605,6 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.active = false;
     return;
   }
-  const U4 w = philox4x32_10(j, pid, 1u, a.instance, keys.rk);
   const int32_t slot = choose_slot(g, vr, w.x);
   const SlotRec sr = g.slot[slot];
   EdgeRec32 qn{};  // the new edge (binary32 modes)
@@ -1104,9 +1106,11 @@ __device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, in
 
 // The range form of the fused EM-Step kernel: block b runs particles
 // [b range, (b + 1) range) of one set with lanes that claim particles.
+// (binary32 modes: at most 64 registers, four blocks per SM, like the tile
+// kernel; binary64 unconstrained.)
 template <int kMode>
-__global__ void __launch_bounds__(256) em_range_kernel(const __grid_constant__ SimArgs a,
-                                                       const __grid_constant__ Keys keys) {
+__global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
+    em_range_kernel(const __grid_constant__ SimArgs a, const __grid_constant__ Keys keys) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RangeCtl ctl;
   const int64_t lo = (int64_t)blockIdx.x * a.range;
