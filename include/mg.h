@@ -130,8 +130,8 @@ mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge, uint8
 
 /* Creates a set of n particles on g (1 <= n <= 2^31 - 1).  edge0[n], x0[n]:
  * starting edges and positions, host arrays, or device arrays when
- * inputs_on_device != 0; 0 <= x0 <= l_e (x0 = 0 or l_e starts the particle at
- * that vertex).  Particle i has the global id pid = pid_base + i (must not
+ * inputs_on_device != 0; 0 <= x0 <= l_e and finite (x0 = 0 or l_e starts the
+ * particle at that vertex; a semi-infinite edge has no far vertex).  Particle i has the global id pid = pid_base + i (must not
  * wrap 2^32).  Its random numbers are Philox-4x32-10 (Salmon et al., SC'11)
  * blocks under the key (seed mod 2^32, seed >> 32):
  *   the n-th normal (one per Euler-Maruyama sub-step -- the first of a step

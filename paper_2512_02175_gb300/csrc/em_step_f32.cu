@@ -157,7 +157,7 @@ __global__ void init_state_kernel(GraphView g, const int32_t* __restrict__ edge0
     const double x = x0[i];
     uint32_t bad = 0;
     if (e < kDead || e >= g.E) bad |= kErrBadEdge;
-    else if (e >= 0 && !(x >= 0.0 && x <= g.e64[e].L)) bad |= kErrNan;
+    else if (e >= 0 && !(x >= 0.0 && x <= g.e64[e].L && isfinite(x))) bad |= kErrNan;
     if (bad) atomicOr(err, bad);
     s.edge[i] = e;
     if (f64) reinterpret_cast<double*>(s.x)[i] = x;

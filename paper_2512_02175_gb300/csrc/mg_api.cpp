@@ -407,8 +407,9 @@ mg_status load_positions(mg_particles p, const int32_t* edge0, const double* x0,
       if (e < 0 || e >= g->E)
         return fail(MG_ERR_INVALID_ARG, "particle %lld: edge %d out of range", (long long)i, e);
       const double x = x0[i];
-      if (!(x >= 0.0 && x <= g->length[e]))
-        return fail(MG_ERR_INVALID_ARG, "particle %lld: x0 outside [0, l_e]", (long long)i);
+      if (!(x >= 0.0 && x <= g->length[e] && std::isfinite(x)))
+        return fail(MG_ERR_INVALID_ARG, "particle %lld: x0 outside [0, l_e] or not finite",
+                    (long long)i);
     }
     // edges straight into place; positions into the 8n bytes of hits and
     // first_hits (binary64 staging), converted by the init kernel
@@ -1088,7 +1089,7 @@ extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const dou
   for (size_t i = 0; i < n; ++i) {
     const int32_t e = edge[i];
     if (e < -1 || e >= g->E) return fail(MG_ERR_INVALID_ARG, "edge out of range");
-    if (e >= 0 && !(x[i] >= 0.0 && x[i] <= g->length[e]))
+    if (e >= 0 && !(x[i] >= 0.0 && x[i] <= g->length[e] && std::isfinite(x[i])))
       return fail(MG_ERR_INVALID_ARG, "x outside [0, l_e]");
   }
   std::vector<float> xf;

@@ -824,7 +824,7 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
       const R x0 = p.x;
       enter_edge<kMode>(p, g, p.e, a);
       p.x = x0;
-      if (!(p.x >= R(0) && p.x <= p.L)) {
+      if (!(p.x >= R(0) && p.x <= p.L && isfinite(p.x))) {  // finite: L may be +inf
         atomicOr(a.c.err, kErrNan);
         ok = false;
       }
@@ -968,7 +968,7 @@ __device__ __forceinline__ bool load_particle(Lane<kMode>& p, uint32_t& pid, con
     const R x0 = p.x;
     enter_edge<kMode>(p, g, p.e, a);
     p.x = x0;
-    if (!(p.x >= R(0) && p.x <= p.L)) {
+    if (!(p.x >= R(0) && p.x <= p.L && isfinite(p.x))) {  // finite: L may be +inf
       atomicOr(a.c.err, kErrNan);
       ok = false;
     }

@@ -357,6 +357,24 @@ def test_device_inputs_and_validation(B):
         B.Particles(g, np.array([0, 99], np.int32), np.array([0.1, 0.1]), seed=3)
     assert ei.value.status == B.MG_ERR_INVALID_ARG
     g.close()
+    # a position at +inf on a semi-infinite edge (x <= l_e = inf holds) is
+    # rejected: on the host, and as a device error for device input, in
+    # every mode
+    d = W.paper_star("linear")
+    g = B.Graph(d)
+    with pytest.raises(B.MGError) as ei:
+        B.Particles(g, np.array([0, 1], np.int32), np.array([0.1, np.inf]), seed=3)
+    assert ei.value.status == B.MG_ERR_INVALID_ARG
+    for prec in (B.MG_FP64, B.MG_FP32_MIXED, B.MG_FP32):
+        p = B.Particles(g, torch.tensor([0, 1], dtype=torch.int32, device="cuda"),
+                        torch.tensor([0.1, np.inf], dtype=torch.float64, device="cuda"),
+                        seed=3, precision=prec)
+        with pytest.raises(B.MGError) as ei:
+            p.simulate(1e-3, 10, 8)
+            p.synchronize()
+        assert ei.value.status == B.MG_ERR_DEVICE_FAULT
+        p.close()
+    g.close()
 
 
 def test_torch_allocator_same_results(B):
