@@ -60,7 +60,8 @@ typedef enum { MG_VERTEX_STANDARD = 0, MG_VERTEX_ABSORBING = 1 } mg_vertex_kind;
 
 /* Device-error bits reported with MG_ERR_DEVICE_FAULT. */
 #define MG_DEVERR_BAD_EDGE 1u  /* a particle's edge index out of range */
-#define MG_DEVERR_NAN 2u       /* a position became NaN or left [0, l_e] */
+#define MG_DEVERR_NAN 2u       /* a position was NaN, infinite or outside [0, l_e], or
+                                  overflowed to infinity (the particle stops) */
 #define MG_DEVERR_STREAM 4u    /* a particle used up its 2^32 - 16 normals */
 #define MG_DEVERR_STUCK 8u     /* the kernel's loop guard fired (a library bug) */
 

@@ -598,6 +598,13 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   p.hits = j + 1u;
   if (!p.at_v) p.first_hits++;
   p.k++;
+  if (v < 0) {
+    // the far end of a semi-infinite edge: only an end point that overflowed
+    // to +inf gets here (a drift pushing the particle off to infinity)
+    atomicOr(a.c.err, kErrNan);
+    p.active = false;
+    return;
+  }
   const VtxRec vr = g.vtx[v];
   if (vr.kind == kVertexAbsorbing) {
     count_absorbed(a.c, bc, v);

@@ -377,6 +377,26 @@ def test_device_inputs_and_validation(B):
     g.close()
 
 
+def test_overflow_to_infinity_is_reported(B):
+    """A drift that pushes particles off to infinity on a semi-infinite edge
+    (mu = +50 x: x grows by 5% a step) overflows binary32 within ~1800 steps:
+    the kernel stops those particles and reports a device error instead of
+    treating the overflow as a hit at the edge's missing far end."""
+    d = W.paper_star("quadratic", k=2)
+    d = dict(d, c1=np.array([50.0, -10.0]))
+    g = B.Graph(d)
+    e = np.array([0] * 64 + [1] * 64, np.int32)
+    x = np.full(128, 1.0)
+    for prec in (B.MG_FP32_MIXED, B.MG_FP32):
+        p = B.Particles(g, e, x, seed=1, precision=prec)
+        with pytest.raises(B.MGError) as ei:
+            p.simulate(1e-3, 4000, 8)
+            p.synchronize()
+        assert ei.value.status == B.MG_ERR_DEVICE_FAULT
+        p.close()
+    g.close()
+
+
 def test_torch_allocator_same_results(B):
     d = W.star_brownian(3)
     e, x = W.round_robin_uniform(d, 2000, 3)
