@@ -9,25 +9,30 @@
 // Every Euler-Maruyama sub-step -- the first of a step, and each one that
 // continues a step from a vertex after a split -- takes the next normal of
 // the particle's own counter-based stream (Philox-4x32-10 + Box-Muller, four
-// normals per block), buffered per thread in a ring in shared memory.  The
-// loop runs in quads; per lane and quad:
+// normals per block), buffered per thread in a ring of 16 in shared memory.
+// A warp loops in iterations; per lane and iteration:
 //
-//   vertex    a lane sitting at a vertex (after a split, or at the start of a
-//             step) takes its one sub-step from the vertex: W = +-|z| into the
-//             edge, over the time left h;
-//   interior  then up to four sub-steps x~ = x + mu_e(x) dt + sigma_e
-//             sqrt(dt) z, two FMAs and a range test each, with no other
-//             bookkeeping;
-//   split     a sub-step that ends outside (0, l_e) leaves the lane pending.
-//             The warp resolves its pending lanes together -- once enough are
-//             waiting, or when no other lane can move -- so the long split path
-//             (hitting fraction, time left, jump draw, next edge) runs with
-//             many lanes active instead of one.  A particle's draws depend
-//             only on its own counters, so batching does not change results.
+//   split     a lane whose last sub-step ended outside (0, l_e) is pending;
+//             the warp resolves its pending lanes together in one pass --
+//             hitting fraction, time left, jump draw, next edge, and the
+//             sub-step from the vertex, repeated while it hits again -- so
+//             the long split path runs with many lanes active instead of one.
+//             A particle's draws depend only on its own counters, so batching
+//             does not change results;
+//   refill    the ring is topped up to at least kSub + 1 normals;
+//   vertex    a lane sitting at a vertex at the start of a step takes its
+//             sub-step from the vertex: W = +-|z| into the edge;
+//   interior  then kSub sub-steps (8 in the binary32 modes, 4 in binary64)
+//             x~ = x + mu_e(x) dt + sigma_e sqrt(dt) z, two FMAs and a range
+//             test each, branch-free; the first that leaves (0, l_e) makes
+//             the lane pending.
 //
 // Counters (exits per slot, absorptions, truncations) and the optional
 // snapshot histogram are privatised in shared memory when they fit and
-// flushed with one atomic per nonzero entry per block.
+// flushed with one atomic per nonzero entry per block.  em_step_kernel runs
+// one particle per thread; em_range_kernel (graphs whose particles can die)
+// lets a lane claim the next particle of its block's range when its own
+// dies or finishes; em_batch_kernel runs 256-particle tiles of many sets.
 //
 // Precision modes (template kMode):
 //   kModeF64    everything in binary64, in the same operation order as the
@@ -494,7 +499,7 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
 // decides which ones count.  Ring rows past the lane's generated normals may
 // be read (in bounds: at most kRing - 1 + kSub - 1 < 2 kRing) but never count.
 template <int kMode, bool kCheckLeft>
-__device__ __forceinline__ void interior_quad(Lane<kMode>& p, const typename Types<kMode>::R* ring,
+__device__ __forceinline__ void interior_sub_steps(Lane<kMode>& p, const typename Types<kMode>::R* ring,
                                               bool run) {
   using R = typename Types<kMode>::R;
   constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
@@ -769,8 +774,8 @@ __device__ __forceinline__ void iteration(Lane<kMode>& p, const GraphView& g, co
   constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
   if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
   const bool run = p.active && !p.pending && !p.at_v;
-  if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
-  else interior_quad<kMode, true>(p, ring, run);
+  if (__all_sync(full, !run || p.left >= kSub)) interior_sub_steps<kMode, false>(p, ring, run);
+  else interior_sub_steps<kMode, true>(p, ring, run);
 }
 
 // One block's tile of a particle set: particle i of the calling thread
@@ -860,18 +865,18 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
 
   // Iterations of at most kSub + 1 sub-steps per lane (one from a vertex,
   // kSub interior); pending vertex hits resolved in warp-wide batches (split_batch
-  // lanes, or whenever nothing else moves).  Every quad moves some lane
+  // lanes, or whenever nothing else moves).  Every iteration moves some lane
   // forward by a sub-step or a split, and a lane has at most 2M + 1 of those
-  // per step, so the loop ends within 32 steps (2M + 2) quads; the cap turns a
+  // per step, so the loop ends within 32 steps (2M + 2) iterations; the cap turns a
   // logic error into a reported fault instead of a hang (the host keeps it
   // within 32 bits).
   const uint32_t full = 0xffffffffu;
   const uint32_t cap = 32u * (uint32_t)a.steps * (uint32_t)(2 * a.M + 2) + 64u;
-  uint32_t quads = 0;
+  uint32_t iters = 0;
   for (;;) {
     const uint32_t am = __ballot_sync(full, p.active);
     if (am == 0u) break;
-    if (++quads > cap) {
+    if (++iters > cap) {
       if (p.active) atomicOr(a.c.err, kErrStuck);
       break;
     }
@@ -894,8 +899,8 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
     constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
     if (p.active && !p.pending && p.at_v) vertex_sub_step<kMode>(p, ring, a, bc);
     const bool run = p.active && !p.pending && !p.at_v;
-    if (__all_sync(full, !run || p.left >= kSub)) interior_quad<kMode, false>(p, ring, run);
-    else interior_quad<kMode, true>(p, ring, run);
+    if (__all_sync(full, !run || p.left >= kSub)) interior_sub_steps<kMode, false>(p, ring, run);
+    else interior_sub_steps<kMode, true>(p, ring, run);
   }
 
   if (ok && i < a.n) {
@@ -1070,11 +1075,11 @@ __device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, in
 
   // As in run_tile, plus: between two iterations in which a lane of the warp
   // takes a new particle, every iteration moves one of the at most 32
-  // particles held by a sub-step or a split, so `quads`, restarted whenever a
+  // particles held by a sub-step or a split, so `iters`, restarted whenever a
   // lane takes a particle, stays within 32 steps (2M + 2) + 64.
   const uint32_t full = 0xffffffffu;
   const uint32_t cap = 32u * (uint32_t)a.steps * (uint32_t)(2 * a.M + 2) + 64u;
-  uint32_t quads = 0;
+  uint32_t iters = 0;
   for (;;) {
     bool took = false;
     if (!p.active && claim) {
@@ -1091,10 +1096,10 @@ __device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, in
         held = load_particle<kMode>(p, pid, a, keys, g, blk.ring, blk.shist, nx);
       } while (!held);
     }
-    if (__any_sync(full, took)) quads = 0;
+    if (__any_sync(full, took)) iters = 0;
     const uint32_t am = __ballot_sync(full, p.active);
     if (am == 0u) break;
-    if (++quads > cap) {
+    if (++iters > cap) {
       if (p.active) atomicOr(a.c.err, kErrStuck);
       break;
     }
