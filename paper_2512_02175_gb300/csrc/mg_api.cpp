@@ -556,9 +556,10 @@ struct Plan {
   mg::SimArgs a{};
   bool f64 = false, stage = true, counters = true, shist = false;
   int32_t hist_len = 0;
+  int32_t counter_bytes = 4;  // 8 for the range kernel
   size_t smem(bool with_hist, const mg_graph g) const {
     return mg::smem_layout(g->V, g->E, g->S, g->view.G, f64, stage, counters,
-                           (with_hist && shist) ? hist_len : 0, mg::kBlock).total;
+                           (with_hist && shist) ? hist_len : 0, mg::kBlock, counter_bytes).total;
   }
 };
 
@@ -664,9 +665,12 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   int64_t first = std::min(steps, max_steps_per_launch(M, false));
   if (p->steps_per_launch > 0) first = std::min(first, p->steps_per_launch);
   pl.a.range = block_range(p, pl.smem(true, g), first);
-  if (pl.a.range > mg::kBlock) {  // blocks run many particles: 64-bit global counters
-    pl.counters = false;
-    pl.a.smem_counters = 0;
+  if (pl.a.range > mg::kBlock) {  // blocks run many particles: 64-bit counters
+    pl.counter_bytes = 8;
+    if (pl.counters && pl.smem(true, g) > kSmemBudget + 128u * mg::kBlock) {
+      pl.counters = false;
+      pl.a.smem_counters = 0;
+    }
   }
   int64_t chunk = max_steps_per_launch(M, pl.counters);
   if (p->steps_per_launch > 0 && p->steps_per_launch < chunk) chunk = p->steps_per_launch;

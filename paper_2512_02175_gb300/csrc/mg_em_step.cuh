@@ -217,22 +217,26 @@ __device__ __forceinline__ int32_t choose_slot(const GraphView& g, const VtxRec&
 }
 
 // Exit and absorption counters of a block, privatised in shared memory when
-// they fit (32-bit: a tile of 256 particles cannot overflow them within one
-// launch; the range kernel, whose blocks run many particles, counts in
-// global memory).
-struct BlockCounters {
-  uint32_t* exits;     // shared [S] or nullptr (then global atomics)
-  uint32_t* absorbed;  // shared [V] or nullptr
+// they fit: 32-bit for a tile of 256 particles (one launch cannot overflow
+// them), 64-bit for the range kernel, whose blocks run many particles.
+template <typename C>
+struct BlockCountersT {
+  C* exits;     // shared [S] or nullptr (then global atomics)
+  C* absorbed;  // shared [V] or nullptr
 };
+using BlockCounters = BlockCountersT<uint32_t>;
+using BlockCounters64 = BlockCountersT<unsigned long long>;
 
-__device__ __forceinline__ void count_exit(const CounterView& c, const BlockCounters& b,
+template <typename C>
+__device__ __forceinline__ void count_exit(const CounterView& c, const BlockCountersT<C>& b,
                                            int32_t slot) {
-  if (b.exits) atomicAdd(&b.exits[slot], 1u);
+  if (b.exits) atomicAdd(&b.exits[slot], (C)1);
   else atomicAdd(&c.exits[slot], 1ull);
 }
-__device__ __forceinline__ void count_absorbed(const CounterView& c, const BlockCounters& b,
+template <typename C>
+__device__ __forceinline__ void count_absorbed(const CounterView& c, const BlockCountersT<C>& b,
                                                int32_t v) {
-  if (b.absorbed) atomicAdd(&b.absorbed[v], 1u);
+  if (b.absorbed) atomicAdd(&b.absorbed[v], (C)1);
   else atomicAdd(&c.absorbed[v], 1ull);
 }
 
@@ -468,10 +472,10 @@ __device__ __forceinline__ void mark_near_branch(Lane<kMode>& p, typename Types<
 
 // The sub-step of a lane at a vertex: into the edge with |z|; ending inside
 // it is an exit through the vertex slot and closes the step.
-template <int kMode>
+template <int kMode, typename BC>
 __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
                                                 const typename Types<kMode>::R* ring,
-                                                const SimArgs& a, const BlockCounters& bc) {
+                                                const SimArgs& a, const BC& bc) {
   using R = typename Types<kMode>::R;
   const R z = ring[(p.n_draw & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x];
   p.n_draw++;
@@ -540,9 +544,9 @@ __device__ __forceinline__ void interior_sub_steps(Lane<kMode>& p, const typenam
 
 // Resolve the pending vertex hit: partial step to the vertex, time left,
 // jump draw, next edge, and the coefficients of the rest of the step.
-template <int kMode>
+template <int kMode, typename BC>
 __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
-                                      const Keys& keys, const BlockCounters& bc,
+                                      const Keys& keys, const BC& bc,
                                       const typename Types<kMode>::R* ring, uint32_t pid,
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
@@ -684,7 +688,7 @@ __device__ __forceinline__ void block_zero(T* dst, int32_t n) {
 template <int kMode>
 struct BlockSetup {
   GraphView g;
-  BlockCounters bc;
+  BlockCounters64 bc;
   uint32_t* shist;
   int32_t hist_len;
   typename Types<kMode>::R* ring;
@@ -701,7 +705,7 @@ __device__ __forceinline__ BlockSetup<kMode> setup_block(const SimArgs& a, unsig
   GraphView& g = b.g;
   b.hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
   const SmemLayout lay = smem_layout(g.V, g.E, g.S, g.G, kF64, a.stage_smem, a.smem_counters,
-                                     b.hist_len, kThreads);
+                                     b.hist_len, kThreads, 8);
   if (a.stage_smem) {
     if constexpr (kF64) {
       block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
@@ -717,10 +721,10 @@ __device__ __forceinline__ BlockSetup<kMode> setup_block(const SimArgs& a, unsig
     g.vtx = reinterpret_cast<const VtxRec*>(smem + lay.vtx);
     g.guide = reinterpret_cast<const int32_t*>(smem + lay.guide);
   }
-  b.bc = BlockCounters{nullptr, nullptr};
+  b.bc = BlockCounters64{nullptr, nullptr};
   if (a.smem_counters) {
-    b.bc.exits = reinterpret_cast<uint32_t*>(smem + lay.exits);
-    b.bc.absorbed = reinterpret_cast<uint32_t*>(smem + lay.absorbed);
+    b.bc.exits = reinterpret_cast<unsigned long long*>(smem + lay.exits);
+    b.bc.absorbed = reinterpret_cast<unsigned long long*>(smem + lay.absorbed);
     block_zero(b.bc.exits, g.S);
     block_zero(b.bc.absorbed, g.V);
   }
@@ -737,9 +741,9 @@ __device__ __forceinline__ void flush_block(const SimArgs& a, const BlockSetup<k
   __syncthreads();
   if (a.smem_counters) {
     for (int32_t k = threadIdx.x; k < b.g.S; k += blockDim.x)
-      if (b.bc.exits[k]) atomicAdd(&a.c.exits[k], (unsigned long long)b.bc.exits[k]);
+      if (b.bc.exits[k]) atomicAdd(&a.c.exits[k], b.bc.exits[k]);
     for (int32_t k = threadIdx.x; k < b.g.V; k += blockDim.x)
-      if (b.bc.absorbed[k]) atomicAdd(&a.c.absorbed[k], (unsigned long long)b.bc.absorbed[k]);
+      if (b.bc.absorbed[k]) atomicAdd(&a.c.absorbed[k], b.bc.absorbed[k]);
   }
   if (b.shist)
     for (int32_t k = threadIdx.x; k < b.hist_len; k += blockDim.x)
@@ -749,9 +753,9 @@ __device__ __forceinline__ void flush_block(const SimArgs& a, const BlockSetup<k
 // One iteration of a warp after its liveness check: the split pass (each
 // pending lane's whole chain of vertex hits), the refills, the sub-step from
 // a vertex, and kSub interior sub-steps.
-template <int kMode>
+template <int kMode, typename BC>
 __device__ __forceinline__ void iteration(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
-                                          const Keys& keys, const BlockCounters& bc,
+                                          const Keys& keys, const BC& bc,
                                           typename Types<kMode>::R* ring, uint32_t pid,
                                           uint32_t& trunc, uint32_t am) {
   const uint32_t full = 0xffffffffu;
@@ -1052,7 +1056,7 @@ __device__ __forceinline__ void finish_particle(const Lane<kMode>& p, uint32_t p
 template <int kMode>
 __device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, int64_t lo,
                                           int64_t hi, unsigned char* smem, RangeCtl* ctl) {
-  const BlockSetup<kMode> blk = setup_block<kMode>(a, smem);  // a.smem_counters == 0
+  const BlockSetup<kMode> blk = setup_block<kMode>(a, smem);
   const GraphView& g = blk.g;
   if (threadIdx.x == 0) {
     ctl->next = (unsigned long long)(lo + blockDim.x);
@@ -1143,8 +1147,10 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
 // of one instance -- from a queue (ordered longest first by the host) until
 // it is empty, copying the instance's arguments to shared memory and running
 // the same tile body, so a particle's result does not depend on the batch.
+// (binary32 modes: at most 64 registers, four blocks per SM.)
 template <int kMode>
-__global__ void __launch_bounds__(256) em_batch_kernel(const SimArgs* __restrict__ insts,
+__global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
+    em_batch_kernel(const SimArgs* __restrict__ insts,
                                                        const BatchItem* __restrict__ items,
                                                        int32_t n_items, uint32_t* head,
                                                        const __grid_constant__ Keys keys) {

@@ -117,7 +117,8 @@ struct SmemLayout {
 MG_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, int32_t G, bool f64,
-                                    bool stage, bool counters, int32_t hist_len, int32_t block) {
+                                    bool stage, bool counters, int32_t hist_len, int32_t block,
+                                    int32_t counter_bytes = 4) {
   SmemLayout l{};
   size_t off = 0;
   l.ring = off;  // buffered normals, each stored twice: 32 KB at 256 threads
@@ -128,9 +129,9 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, int32_t G, 
     l.vtx = off; off += align16((size_t)V * sizeof(VtxRec));
     l.guide = off; off += align16((size_t)G * sizeof(int32_t));
   }
-  if (counters) {
-    l.exits = off; off += align16((size_t)S * 4);
-    l.absorbed = off; off += align16((size_t)V * 4);
+  if (counters) {  // 4-byte (tiles) or 8-byte (range kernel) counters
+    l.exits = off; off += align16((size_t)S * counter_bytes);
+    l.absorbed = off; off += align16((size_t)V * counter_bytes);
   }
   l.hist = off;
   off += align16((size_t)hist_len * 4);
