@@ -84,6 +84,37 @@ def test_star3_brownian_fp64_trajectories(B):
     assert gc["exits"].sum() > 100_000
 
 
+def test_star3_fp64_matches_golden_values(B):
+    """The FP64 kernel against the stored oracle values of tests/golden/
+    (the 3-edge Brownian star, 48 particles, 400 steps): same edges, draw and
+    hit counters, histogram and exit counts; positions within 1e-12."""
+    import json
+    import os
+    from tests.golden import make_golden
+    with open(os.path.join(os.path.dirname(__file__), "golden", "star3_brownian.json")) as f:
+        gold = json.load(f)
+    c = gold["case"]
+    e, x = make_golden.initial(c["n"])
+    g = B.Graph(make_golden.star3())
+    p = B.Particles(g, e, x, seed=c["seed"], instance=c["instance"], precision=B.MG_FP64)
+    p.simulate(c["dt"], c["steps"], c["M"])
+    p.synchronize()
+    st, cn = p.state(), p.counts()
+    hist = p.histogram(c["bins"])
+    p.close()
+    g.close()
+    assert not np.any(st["flags"] & 1)
+    assert st["edge"].tolist() == gold["edge"]
+    assert st["n_draw"].tolist() == gold["n_draw"]
+    assert st["hits"].tolist() == gold["hits"]
+    assert st["first_hits"].tolist() == gold["first_hits"]
+    xg = np.array([float.fromhex(v) for v in gold["x"]])
+    assert np.max(np.abs(st["x"] - xg)) <= 1e-12
+    assert hist.tolist() == gold["histogram"]
+    assert cn["exits"].tolist() == gold["exits"]
+    assert cn["particle_steps"] == gold["particle_steps"]
+
+
 def test_mixed_graph_fp64_unaligned_chunks(B):
     """Cycles, a self-loop, a semi-infinite edge, zero weights, absorbing
     vertices, a small split cap (truncations), ids offset, steps in chunks
