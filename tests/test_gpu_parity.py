@@ -553,6 +553,56 @@ def test_vascular_fp64_trajectories(B):
     assert gc["absorbed"].sum() > 0
 
 
+def test_vascular_full_size_sampled(B):
+    """The vascular configuration at full size (2^26 tracers, 2000 steps,
+    M = 32, FP32-mixed: the range kernel): every tracer counted once (alive
+    in the histogram or absorbed), positions inside their edges, and the
+    absorbed fraction equal to an oracle sample's within 4 standard errors;
+    then FP64 at full N over 800 steps (also the range kernel) against
+    oracle trajectories of 512 sampled tracers."""
+    import torch
+    d = W.vascular()
+    n = 1 << 26
+    e, x = W.inject_at_inlets(d, n, 11)
+    g = B.Graph(d)
+    h = torch.zeros(g.n_edges * 16, dtype=torch.int32, device="cuda")
+    p = B.Particles(g, e, x, seed=0, precision=B.MG_FP32_MIXED)
+    p.simulate(d["dt"], 2000, 32, hist_bins=16, hist_out=h)
+    p.synchronize()
+    st, cnt = p.state(), p.counts()
+    p.close()
+    alive = st["edge"] >= 0
+    hist = h.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert hist.sum() == alive.sum()
+    assert hist.sum() + cnt["absorbed"].sum() == n
+    # binary32 state: an edge's length is its binary32 rounding (a tracer at
+    # the far vertex sits at float(l_e), which may exceed l_e)
+    L = np.asarray(d["length"]).astype(np.float32).astype(np.float64)[st["edge"][alive]]
+    assert np.all((st["x"][alive] >= 0) & (st["x"][alive] <= L))
+    idx = np.sort(np.random.default_rng(7).choice(n, 1024, replace=False))
+    o = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=d["dt"], steps=2000, M=32)
+    pg = 1.0 - alive.mean()
+    po = np.mean(o["edge"] < 0)
+    assert abs(pg - po) <= 4 * np.sqrt(pg * (1 - pg) / len(idx)) + 1e-9, (pg, po)
+    # FP64 at full N over 800 steps: the sampled trajectories exactly
+    p = B.Particles(g, e, x, seed=0, precision=B.MG_FP64)
+    p.simulate(d["dt"], 800, 32)
+    p.synchronize()
+    s64 = p.state()
+    p.close()
+    g.close()
+    idx = idx[:512]
+    o64 = oracle_pool.run(d, e[idx], x[idx], idx, seed=0, dt=d["dt"], steps=800, M=32)
+    sub = {k: s64[k][idx] for k in ("edge", "x", "n_draw", "hits", "flags")}
+    ok = ((sub["flags"] | o64["flags"]) & 1) == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(sub["edge"][ok], o64["edge"][ok])
+    assert np.array_equal(sub["n_draw"][ok], o64["n_draw"][ok])
+    assert np.array_equal(sub["hits"][ok], o64["hits"][ok])
+    live = ok & (o64["edge"] >= 0)
+    assert np.all(np.abs(sub["x"][live] - o64["x"][live]) <= REL * np.maximum(1, np.abs(o64["x"][live])))
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp32"])
 def test_vascular_fp32_statistics(B, prec):
     d = W.vascular(n_points=5000)
