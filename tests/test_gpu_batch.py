@@ -145,3 +145,63 @@ def test_batch_rejects_mixed_seeds_and_precisions(B):
     with pytest.raises(B.MGError):
         b.add(p1, 1e-3, 10, 8)
     b.close()
+
+
+def test_full_size_batch_sampled(B):
+    """The batched configuration at full size, in the launch the benchmark
+    times: all 512 instances (3.3e8 particles, 100..5000 steps each) in one
+    graph-replayed persistent launch, FP32-mixed -- every instance takes all
+    its particle-steps (no vertex absorbs) and stays on its edges; then the
+    same 512 instances in FP64 over a tenth of their steps, 8 sampled
+    particles of every 32nd instance against the oracle, trajectory by
+    trajectory."""
+    import torch
+    insts = W.batch_instances(512)
+    s = torch.cuda.Stream()
+    graphs, parts = [], []
+    for k, it in enumerate(insts):
+        g = B.Graph(it["graph"])
+        e, x = W.uniform_on_edges(it["graph"], it["n"], 100 + k)
+        it["x0"] = (e, x)
+        graphs.append(g)
+        parts.append(B.Particles(g, e, x, seed=0, instance=k, precision=B.MG_FP32_MIXED))
+    b = B.Batch()
+    for p, it in zip(parts, insts):
+        b.add(p, it["dt"], it["steps"], it["M"])
+    b.run(use_graph=True, stream=s)
+    s.synchronize()
+    for p, it, g in zip(parts, insts, graphs):
+        c = p.counts()
+        assert c["particle_steps"] == it["n"] * it["steps"]
+        if it["instance"] % 64 == 0:
+            st = p.state()
+            L = np.asarray(it["graph"]["length"]).astype(np.float32).astype(np.float64)
+            assert np.all((st["x"] >= 0) & (st["x"] <= L[st["edge"]]))
+        p.close()
+    b.close()
+    # FP64, a tenth of the steps, full particle counts
+    parts = [B.Particles(g, *it["x0"], seed=0, instance=k, precision=B.MG_FP64)
+             for k, (g, it) in enumerate(zip(graphs, insts))]
+    b = B.Batch()
+    for p, it in zip(parts, insts):
+        b.add(p, it["dt"], max(1, it["steps"] // 10), it["M"])
+    b.run(use_graph=True, stream=s)
+    s.synchronize()
+    rng = np.random.default_rng(3)
+    for k in range(0, 512, 32):
+        it, p = insts[k], parts[k]
+        st = p.state()
+        idx = np.sort(rng.choice(it["n"], 8, replace=False))
+        e, x = it["x0"]
+        o = oracle_pool.run(it["graph"], e[idx], x[idx], idx, seed=0, instance=k, dt=it["dt"],
+                            steps=max(1, it["steps"] // 10), M=it["M"])
+        ok = ((st["flags"][idx] | o["flags"]) & 1) == 0
+        assert np.array_equal(st["edge"][idx][ok], o["edge"][ok])
+        assert np.array_equal(st["n_draw"][idx][ok], o["n_draw"][ok])
+        assert np.all(np.abs(st["x"][idx][ok] - o["x"][ok])
+                      <= 1e-12 * np.maximum(1.0, np.abs(o["x"][ok])))
+    for p in parts:
+        p.close()
+    b.close()
+    for g in graphs:
+        g.close()
