@@ -71,7 +71,9 @@ class _Active:
 
 class Server:
     def __init__(self, backend, mem_budget: int, n_lanes: int = 2, chunk_steps: int = 500,
-                 max_members: int = 512, clock=time.perf_counter, keep_state: bool = False):
+                 max_members: int = 512, clock=time.perf_counter, keep_state=False):
+        """keep_state: return every request's final particle state (True), none
+        (False), or those of the request ids in a given set."""
         self.backend = backend
         self.mem_budget = int(mem_budget)
         self.n_lanes = n_lanes
@@ -114,7 +116,9 @@ class Server:
             for act, _ in members:
                 act.in_flight = False
                 if act.remaining == 0:
-                    hist, counts, state = self.backend.collect(act.handle, self.keep_state)
+                    keep = (act.req.rid in self.keep_state
+                            if isinstance(self.keep_state, (set, frozenset)) else bool(self.keep_state))
+                    hist, counts, state = self.backend.collect(act.handle, keep)
                     self.backend.release(act.handle)
                     self.reserved -= self.backend.bytes_of(act.req)
                     self.active.remove(act)

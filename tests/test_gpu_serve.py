@@ -58,3 +58,43 @@ def test_plain_path_runs():
     res = serve.serve_plain(reqs, graphs, 0, seed=7)
     assert len(res) == len(reqs)
     assert all(r.particle_steps > 0 for r in res)
+
+
+def test_full_size_trace_sampled():
+    """The served configuration at full size, as the benchmark runs it: 634
+    requests in 3 s over the 3-edge star, the 16-edge star and the full
+    vascular network (n = 2^U[12, 18]), 32 GB admission budget, rounds of 500
+    steps on two streams -- every request completes, and a dozen sampled
+    requests are bit-identical to running them alone."""
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    graphs = {"star3": W.star_brownian(3), "star16": W.star_langevin(16),
+              "vascular": W.vascular()}
+    reqs = serve.poisson_trace(200.0, 3.0, 17, graphs, n_range=(12, 18),
+                               init=serve.default_init)
+    assert len(reqs) > 500
+    sample = set(np.random.default_rng(1).choice(len(reqs), 12, replace=False).tolist())
+    be = serve.GpuBackend(graphs, B.MG_FP32_MIXED, seed=0, n_lanes=2)
+    srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500, keep_state=sample)
+    res = srv.run_trace(reqs, time_limit=600)
+    be.close()
+    assert sorted(r.rid for r in res) == list(range(len(reqs)))
+    by = {r.rid: r for r in res}
+    G = {k: B.Graph(d) for k, d in graphs.items()}
+    for rid in sorted(sample):
+        q = reqs[rid]
+        p = B.Particles(G[q.graph], q.edge0, q.x0, seed=0, instance=q.rid,
+                        precision=B.MG_FP32_MIXED)
+        p.simulate(q.dt, q.steps, q.M)
+        st, cn, h = p.state(), p.counts(), p.histogram(q.bins)
+        p.close()
+        r = by[rid]
+        assert r.state is not None
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+            assert np.array_equal(st[k], r.state[k]), (rid, k)
+        assert np.array_equal(cn["exits"], r.counts["exits"])
+        assert np.array_equal(h, r.hist)
+    assert all(r.state is None for r in res if r.rid not in sample)
+    for g in G.values():
+        g.close()
