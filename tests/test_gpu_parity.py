@@ -183,6 +183,37 @@ def test_edge_cases_fp64(B):
     assert np.all(gs["edge"] == -1) and gc["absorbed"].sum() == 999
 
 
+def test_largest_particle_ids_fp64(B):
+    """Particle ids at the top of the 32-bit range (pid_base + n = 2^32): the
+    random streams are keyed by the global id, so these particles follow the
+    oracle's trajectories like any others (FP64), and in the binary32 modes
+    equal the same particles inside a larger set; a set whose ids would wrap
+    is rejected."""
+    d = W.random_mixed(7)
+    e, x = W.uniform_on_edges(d, 4096, 9)
+    base = (1 << 32) - 4096
+    pid = np.arange(base, base + 4096, dtype=np.uint64).astype(np.uint32)
+    o = oracle_pool.run(d, e, x, pid, seed=11, dt=2e-3, steps=150, M=8)
+    gs, gc, _ = gpu_run(B, d, e, x, seed=11, dt=2e-3, steps=150, M=8, prec=B.MG_FP64,
+                        pid_base=base)
+    assert_fp64_parity(gs, gc, o)
+    # binary32 modes: the same particles alone at the top ids and as the upper
+    # half of a set starting 4096 ids lower give bit-identical results
+    e2 = np.concatenate([e, e])
+    x2 = np.concatenate([x, x])
+    for prec in (B.MG_FP32_MIXED, B.MG_FP32):
+        a, _, _ = gpu_run(B, d, e, x, seed=11, dt=2e-3, steps=150, M=8, prec=prec, pid_base=base)
+        b, _, _ = gpu_run(B, d, e2, x2, seed=11, dt=2e-3, steps=150, M=8, prec=prec,
+                          pid_base=base - 4096)
+        for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+            assert np.array_equal(a[k], b[k][4096:]), k
+    g = B.Graph(d)
+    with pytest.raises(B.MGError) as ei:
+        B.Particles(g, e, x, pid_base=base + 1, seed=11)
+    assert ei.value.status == B.MG_ERR_INVALID_ARG
+    g.close()
+
+
 # ------------------------------------------------------------ invariances
 
 MODES = {"fp64": 0, "mixed": 1, "fp32": 2}
