@@ -132,7 +132,8 @@ mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge, uint8
 /* Creates a set of n particles on g (1 <= n <= 2^31 - 1).  edge0[n], x0[n]:
  * starting edges and positions, host arrays, or device arrays when
  * inputs_on_device != 0; 0 <= x0 <= l_e and finite (x0 = 0 or l_e starts the
- * particle at that vertex; a semi-infinite edge has no far vertex).  Particle i has the global id pid = pid_base + i (must not
+ * particle at that vertex; a semi-infinite edge has no far vertex).  Host
+ * arrays have been copied when the call returns (pinned memory included).  Particle i has the global id pid = pid_base + i (must not
  * wrap 2^32).  Its random numbers are Philox-4x32-10 (Salmon et al., SC'11)
  * blocks under the key (seed mod 2^32, seed >> 32):
  *   the n-th normal (one per Euler-Maruyama sub-step -- the first of a step
@@ -156,7 +157,9 @@ mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edge0, const d
 
 /* Re-initialises the positions of an existing set (same n, graph, seed,
  * precision) from edge0/x0 as in mg_particles_init, and zeroes its per-particle
- * counters, step counter and global counters. */
+ * counters, step counter and global counters.  Host inputs are checked before
+ * anything changes (MG_ERR_INVALID_ARG leaves the set as it was) and have been
+ * copied when the call returns; device inputs are read stream-ordered. */
 mg_status mg_particles_reset(mg_particles p, const int32_t* edge0, const double* x0,
                              int inputs_on_device, void* stream);
 

@@ -394,23 +394,34 @@ void counter_layout(mg_particles_s* p) {
 
 size_t counter_bytes(const mg_graph g) { return 8 * ((size_t)g->S + g->V + 2) + 16; }
 
+// Starting edges and positions given in host memory are checked here (those
+// in device memory by the init kernel, which sets the device error word).
+mg_status check_positions(mg_particles p, const int32_t* edge0, const double* x0, int on_device) {
+  if (!edge0 || !x0) return fail(MG_ERR_INVALID_ARG, "edge0 and x0 are required");
+  if (on_device) return MG_OK;
+  const mg_graph g = p->g;
+  for (int64_t i = 0; i < p->n; ++i) {
+    const int32_t e = edge0[i];
+    if (e < 0 || e >= g->E)
+      return fail(MG_ERR_INVALID_ARG, "particle %lld: edge %d out of range", (long long)i, e);
+    const double x = x0[i];
+    if (!(x >= 0.0 && x <= g->length[e] && std::isfinite(x)))
+      return fail(MG_ERR_INVALID_ARG, "particle %lld: x0 outside [0, l_e] or not finite",
+                  (long long)i);
+  }
+  return MG_OK;
+}
+
+// Uploads checked starting positions and launches the init kernels.  Host
+// arrays have been copied when this returns (they may be pinned memory, which
+// an asynchronous copy would still read later).
 mg_status load_positions(mg_particles p, const int32_t* edge0, const double* x0, int on_device,
                          cudaStream_t st) {
   const int64_t n = p->n;
   const mg_graph g = p->g;
-  if (!edge0 || !x0) return fail(MG_ERR_INVALID_ARG, "edge0 and x0 are required");
   const int32_t* dedge = edge0;
   const double* dx = x0;
   if (!on_device) {
-    for (int64_t i = 0; i < n; ++i) {
-      const int32_t e = edge0[i];
-      if (e < 0 || e >= g->E)
-        return fail(MG_ERR_INVALID_ARG, "particle %lld: edge %d out of range", (long long)i, e);
-      const double x = x0[i];
-      if (!(x >= 0.0 && x <= g->length[e] && std::isfinite(x)))
-        return fail(MG_ERR_INVALID_ARG, "particle %lld: x0 outside [0, l_e] or not finite",
-                    (long long)i);
-    }
     // edges straight into place; positions into the 8n bytes of hits and
     // first_hits (binary64 staging), converted by the init kernel
     MG_CUDA(cudaMemcpyAsync(p->sv.edge, edge0, 4 * (size_t)n, cudaMemcpyHostToDevice, st));
@@ -419,6 +430,7 @@ mg_status load_positions(mg_particles p, const int32_t* edge0, const double* x0,
     dx = reinterpret_cast<const double*>(p->sv.hits);
   }
   MG_CUDA(mg::launch_init_state(g->view, dedge, dx, n, p->prec == MG_FP64, p->sv, p->cv.err, st));
+  if (!on_device) MG_CUDA(cudaStreamSynchronize(st));
   return MG_OK;
 }
 
@@ -439,6 +451,13 @@ extern "C" mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edg
   mg_particles p = new mg_particles_s();
   p->g = g;
   p->n = n;
+  {
+    mg_status c = check_positions(p, edge0, x0, inputs_on_device);
+    if (c != MG_OK) {
+      delete p;
+      return c;
+    }
+  }
   p->pid_base = pid_base;
   p->seed = seed;
   p->instance = instance_id;
@@ -470,9 +489,11 @@ extern "C" mg_status mg_particles_init(mg_graph g, int64_t n, const int32_t* edg
 extern "C" mg_status mg_particles_reset(mg_particles p, const int32_t* edge0, const double* x0,
                                         int inputs_on_device, void* stream) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_particles_reset: NULL particles");
+  mg_status s = check_positions(p, edge0, x0, inputs_on_device);  // before changing anything
+  if (s != MG_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   MG_CUDA(cudaMemsetAsync(p->counters.p, 0, counter_bytes(p->g), st));
-  mg_status s = load_positions(p, edge0, x0, inputs_on_device, st);
+  s = load_positions(p, edge0, x0, inputs_on_device, st);
   if (s != MG_OK) return s;
   p->step = 0;
   p->last_stream = st;

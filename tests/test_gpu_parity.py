@@ -418,6 +418,20 @@ def test_device_inputs_and_validation(B):
     with pytest.raises(B.MGError) as ei:
         B.Particles(g, np.array([0, 99], np.int32), np.array([0.1, 0.1]), seed=3)
     assert ei.value.status == B.MG_ERR_INVALID_ARG
+    # a rejected reset leaves the set as it was: state and counters
+    p = B.Particles(g, e, x, seed=3, precision=B.MG_FP64)
+    p.simulate(2e-3, 50, 8)
+    st0, c0 = p.state(), p.counts()
+    bad_e = e.copy()
+    bad_e[5] = 10_000
+    with pytest.raises(B.MGError) as ei:
+        p.reset(bad_e, x)
+    assert ei.value.status == B.MG_ERR_INVALID_ARG
+    st1, c1 = p.state(), p.counts()
+    for k in ("edge", "x", "n_draw", "hits", "step"):
+        assert np.array_equal(st0[k], st1[k]), k
+    assert np.array_equal(c0["exits"], c1["exits"]) and c0["particle_steps"] == c1["particle_steps"]
+    p.close()
     g.close()
     # a position at +inf on a semi-infinite edge (x <= l_e = inf holds) is
     # rejected: on the host, and as a device error for device input, in
