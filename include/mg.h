@@ -13,7 +13,9 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
  *    stream).  Calls that take a stream are stream-ordered and may return
  *    before the GPU work finishes; errors found on the GPU are reported by the
- *    next mg_synchronize or by any call that reads results back.
+ *    next mg_synchronize or by any call that reads results back.  The library
+ *    orders work on one handle only within one stream: a caller that moves a
+ *    handle to another stream orders the two (an event, or a synchronize).
  *  - Device memory is obtained through the allocator set by
  *    mg_set_allocator (default: cudaMalloc/cudaFree).
  *  - Floating-point inputs are IEEE binary64.  Integers are fixed width.
