@@ -8,8 +8,12 @@
  *    error, mg_last_error() returns a message for the calling thread.
  *  - Pointers marked "host" are caller-owned host memory, read (or written)
  *    only during the call.  Pointers marked "device" are caller-owned device
- *    memory on the current CUDA device.  Handles (mg_graph, mg_particles) are
- *    library-owned and freed by their _destroy call.
+ *    memory on the current CUDA device (managed memory and mapped pinned host
+ *    memory qualify).  A device pointer to ordinary host memory or to another
+ *    device's memory, and a host pointer to device memory, are rejected
+ *    (MG_ERR_INVALID_ARG) before anything runs; array lengths are the
+ *    caller's.  Handles (mg_graph, mg_particles) are library-owned and freed
+ *    by their _destroy call.
  *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
  *    stream).  Calls that take a stream are stream-ordered and may return
  *    before the GPU work finishes; errors found on the GPU are reported by the

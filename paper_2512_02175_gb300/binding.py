@@ -154,6 +154,75 @@ def _on_device(a) -> int:
     return int(bool(getattr(a, "is_cuda", False)))
 
 
+# Sizes the library reads or writes through caller pointers are checked here,
+# where the arrays' lengths are known (the C ABI sees bare pointers).  The
+# graph sizes (V, E, S) of every particle set created through this module:
+_set_sizes: dict[int, tuple[int, int, int]] = {}
+
+
+def _sizes(p):
+    """(V, E, S) of particle set p's graph, or None if it was not created here."""
+    return _set_sizes.get(getattr(p, "value", None))
+
+
+def _host_in(a, dtype, n, what):
+    """A C-contiguous host array of `dtype` with exactly n entries."""
+    if _on_device(a):
+        raise ValueError(f"{what} must be a host array")
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.ndim != 1 or (n is not None and a.size != n):
+        raise ValueError(f"{what} must be 1-D with {n} entries (got shape {a.shape})")
+    return a
+
+
+def _host_out(a, dtype, n, what):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"] \
+            or not a.flags["WRITEABLE"]:
+        raise ValueError(f"{what} must be a writeable C-contiguous {np.dtype(dtype).name} host array")
+    if n is not None and a.size < n:
+        raise ValueError(f"{what} needs at least {n} entries (got {a.size})")
+    return a
+
+
+def _device_arr(t, dtypes, n, what, exact=False):
+    """A contiguous CUDA tensor on the current device, of one of `dtypes`
+    (names), with n entries (at least n unless exact)."""
+    import torch
+    if not _on_device(t):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if str(t.dtype).replace("torch.", "") not in dtypes:
+        raise ValueError(f"{what} must have dtype {' or '.join(dtypes)} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what} is on {t.device}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if n is not None and (t.numel() != n if exact else t.numel() < n):
+        raise ValueError(f"{what} needs {'exactly' if exact else 'at least'} {n} entries "
+                         f"(got {t.numel()})")
+    return t
+
+
+_U32 = ("int32", "uint32")
+
+
+def _hist_dev(p, bins, out, what="hist_out"):
+    sz = _sizes(p)
+    return _device_arr(out, _U32, None if sz is None else sz[1] * int(bins), what)
+
+
+def _positions(edge0, x0, n):
+    """edge0 (int32) and x0 (float64) with n entries each, both host or both
+    device; returns (edge0, x0, on_device)."""
+    on_dev = _on_device(x0)
+    if _on_device(edge0) != on_dev:
+        raise ValueError("edge0 and x0 must both be host or both be device arrays")
+    if on_dev:
+        return (_device_arr(edge0, ("int32",), n, "edge0", exact=True),
+                _device_arr(x0, ("float64",), n, "x0", exact=True), 1)
+    return _host_in(edge0, np.int32, n, "edge0"), _host_in(x0, np.float64, n, "x0"), 0
+
+
 # -------------------------------------------------------------- allocator
 
 _torch_hooks = None
@@ -248,29 +317,24 @@ def mg_graph_slots(g):
 def mg_particles_init(g, edge0, x0, *, pid_base=0, seed=0, instance=0, precision=MG_FP64,
                       stream=None):
     """edge0 (int32) and x0 (float64): numpy/CPU arrays or CUDA tensors."""
-    on_dev = _on_device(x0)
-    if _on_device(edge0) != on_dev:
-        raise ValueError("edge0 and x0 must both be host or both be device arrays")
-    if not on_dev:
-        edge0 = np.ascontiguousarray(edge0, dtype=np.int32)
-        x0 = np.ascontiguousarray(x0, dtype=np.float64)
-    n = len(x0)
+    edge0, x0, on_dev = _positions(edge0, x0, len(x0))
+    sizes = mg_graph_info(g)
     h = C.c_void_p()
-    _check(load().mg_particles_init(g, n, _ptr(edge0), _ptr(x0), on_dev, pid_base, seed, instance,
-                                    precision, _stream_ptr(stream), C.byref(h)))
+    _check(load().mg_particles_init(g, len(x0), _ptr(edge0), _ptr(x0), on_dev, pid_base, seed,
+                                    instance, precision, _stream_ptr(stream), C.byref(h)))
+    _set_sizes[h.value] = sizes
     return h
 
 
 def mg_particles_reset(p, edge0, x0, stream=None):
-    on_dev = _on_device(x0)
-    if not on_dev and not hasattr(x0, "data_ptr"):
-        edge0 = np.ascontiguousarray(edge0, dtype=np.int32)
-        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    n = mg_particles_info(p)[0]
+    edge0, x0, on_dev = _positions(edge0, x0, n)
     _check(load().mg_particles_reset(p, _ptr(edge0), _ptr(x0), on_dev, _stream_ptr(stream)))
 
 
 def mg_particles_destroy(p):
     _check(load().mg_particles_destroy(p))
+    _set_sizes.pop(getattr(p, "value", None), None)
 
 
 def mg_particles_set_tuning(p, split_batch=0, steps_per_launch=0, max_blocks=0):
@@ -285,11 +349,15 @@ def mg_particles_info(p):
 
 
 def mg_simulate(p, dt, steps, M, hist_bins=0, hist_out=None, stream=None):
+    if int(hist_bins) > 0:
+        _hist_dev(p, hist_bins, hist_out)
     _check(load().mg_simulate(p, float(dt), int(steps), int(M), int(hist_bins), _ptr(hist_out),
                               _stream_ptr(stream)))
 
 
 def mg_simulate_sampled(p, dt, steps, M, every, hist_bins, hist_out, stream=None):
+    if int(hist_bins) > 0:
+        _hist_dev(p, hist_bins, hist_out)
     _check(load().mg_simulate_sampled(p, float(dt), int(steps), int(M), int(every),
                                       int(hist_bins), _ptr(hist_out), _stream_ptr(stream)))
 
@@ -302,12 +370,13 @@ def mg_histogram(p, bins, out=None, stream=None):
     """Returns a numpy uint32 [E * bins] histogram, or fills the CUDA tensor
     ``out`` (stream-ordered)."""
     if out is not None and _on_device(out):
+        _hist_dev(p, bins, out, "out")
         _check(load().mg_histogram(p, int(bins), _ptr(out), 1, _stream_ptr(stream)))
         return out
     if out is None:
         raise ValueError("pass a host output array (numpy uint32 [E * bins]) or a CUDA tensor")
-    if out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]:
-        raise ValueError("host output must be a C-contiguous uint32 array")
+    sz = _sizes(p)
+    _host_out(out, np.uint32, None if sz is None else sz[1] * int(bins), "out")
     _check(load().mg_histogram(p, int(bins), _ptr(out), 0, _stream_ptr(stream)))
     return out
 
@@ -316,13 +385,18 @@ def mg_histogram_binned(p, bin_offsets, bin_upper, out, stream=None):
     """Variable-width bins: bin_offsets int32 [E + 1], bin_upper float64
     [bin_offsets[-1]]; fills ``out`` (numpy uint32 or a CUDA tensor) with the
     counts (see include/mg.h)."""
-    off = np.ascontiguousarray(bin_offsets, np.int32)
-    up = np.ascontiguousarray(bin_upper, np.float64)
+    sz = _sizes(p)
+    off = _host_in(bin_offsets, np.int32, None if sz is None else sz[1] + 1, "bin_offsets")
+    if off.size < 1:
+        raise ValueError("bin_offsets must have n_edges + 1 entries")
+    up = _host_in(bin_upper, np.float64, None, "bin_upper")
     if len(up) != int(off[-1]):
         raise ValueError("bin_upper must have bin_offsets[-1] entries")
     dev = 1 if _on_device(out) else 0
-    if not dev and (out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]):
-        raise ValueError("host output must be a C-contiguous uint32 array")
+    if dev:
+        _device_arr(out, _U32, max(0, int(off[-1])), "out")
+    else:
+        _host_out(out, np.uint32, max(0, int(off[-1])), "out")
     _check(load().mg_histogram_binned(p, _ptr(off), _ptr(up), _ptr(out), dev, _stream_ptr(stream)))
     return out
 
@@ -330,13 +404,16 @@ def mg_histogram_binned(p, bin_offsets, bin_upper, out, stream=None):
 def mg_histogram_static(p, bins, out, stream=None):
     """The snapshot histogram into the host array ``out`` (uint32 [E * bins])
     without any device allocation by the library (see include/mg.h)."""
-    if out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]:
-        raise ValueError("out must be a C-contiguous uint32 host array")
+    sz = _sizes(p)
+    _host_out(out, np.uint32, None if sz is None else sz[1] * int(bins), "out")
     _check(load().mg_histogram_static(p, int(bins), _ptr(out), _stream_ptr(stream)))
     return out
 
 
 def mg_exit_counts(p, n_slots, n_vertices, stream=None):
+    sz = _sizes(p)
+    if sz is not None and (int(n_slots), int(n_vertices)) != (sz[2], sz[0]):
+        raise ValueError(f"the set's graph has {sz[2]} slots and {sz[0]} vertices")
     ex = np.zeros(n_slots, np.uint64)
     ab = np.zeros(n_vertices, np.uint64)
     tr = np.zeros(1, np.uint64)
@@ -364,7 +441,8 @@ def mg_state_get(p, stream=None):
 
 
 def mg_state_set(p, state, stream=None):
-    a = {k: np.ascontiguousarray(state[k], dtype=dt) for k, dt in
+    n = mg_particles_info(p)[0]
+    a = {k: _host_in(state[k], dt, n, k) for k, dt in
          [("edge", np.int32), ("x", np.float64), ("n_draw", np.uint32), ("hits", np.uint32),
           ("first_hits", np.uint32), ("flags", np.uint32)]}
     _check(load().mg_state_set(p, _ptr(a["edge"]), _ptr(a["x"]), _ptr(a["n_draw"]), _ptr(a["hits"]),
@@ -381,6 +459,8 @@ def mg_batch_create():
 
 
 def mg_batch_add(b, p, dt, steps, M, hist_bins=0, hist_out=None):
+    if int(hist_bins) > 0:
+        _hist_dev(p, hist_bins, hist_out)
     _check(load().mg_batch_add(b, p, float(dt), int(steps), int(M), int(hist_bins),
                                _ptr(hist_out)))
 

@@ -8,8 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mg.h"
@@ -47,6 +49,46 @@ mg_status cuda_fail(cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
+
+// Where a caller's pointer points, as CUDA sees it.  A kernel of the current
+// device may use its device memory, managed memory and mapped pinned host
+// memory; ordinary host memory (an address CUDA does not know) or another
+// device's memory would fault it, so such "device" arguments are rejected.  A
+// "host" argument read or written by the CPU must not be device memory.
+enum class Mem { kHost, kDevice };
+
+mg_status check_memory(const void* ptr, Mem want, const char* what) {
+  if (!ptr) return MG_OK;  // NULL is the caller's check
+  cudaPointerAttributes at{};
+  cudaError_t ce = cudaPointerGetAttributes(&at, ptr);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    // without a usable device nothing is device memory
+    return want == Mem::kHost ? MG_OK : cuda_fail(ce, what);
+  }
+  if (want == Mem::kDevice) {
+    if (at.type == cudaMemoryTypeUnregistered)
+      return fail(MG_ERR_INVALID_ARG, "%s must be device memory, not ordinary host memory", what);
+    if (at.type == cudaMemoryTypeDevice) {
+      int dev = 0;
+      MG_CUDA(cudaGetDevice(&dev));
+      if (at.device != dev)
+        return fail(MG_ERR_INVALID_ARG, "%s is memory of device %d, the current device is %d", what,
+                    at.device, dev);
+    }
+  } else if (at.type == cudaMemoryTypeDevice) {
+    return fail(MG_ERR_INVALID_ARG, "%s must be host memory, not device memory", what);
+  }
+  return MG_OK;
+}
+
+mg_status check_host(std::initializer_list<std::pair<const void*, const char*>> ptrs) {
+  for (const auto& q : ptrs) {
+    mg_status s = check_memory(q.first, Mem::kHost, q.second);
+    if (s != MG_OK) return s;
+  }
+  return MG_OK;
+}
 
 // ---------------------------------------------------------------- memory
 
@@ -134,6 +176,14 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   if (!d->edge_src || !d->edge_dst || !d->length || !d->drift_c0 || !d->drift_c1 || !d->sigma ||
       !d->weight_init || !d->weight_term)
     return fail(MG_ERR_INVALID_ARG, "mg_graph_create: a required array is NULL");
+  {
+    mg_status s = check_host({{d->edge_src, "edge_src"}, {d->edge_dst, "edge_dst"},
+                              {d->length, "length"}, {d->drift_c0, "drift_c0"},
+                              {d->drift_c1, "drift_c1"}, {d->sigma, "sigma"},
+                              {d->weight_init, "weight_init"}, {d->weight_term, "weight_term"},
+                              {d->hist_range, "hist_range"}, {d->vertex_kind, "vertex_kind"}});
+    if (s != MG_OK) return s;
+  }
   for (int32_t e = 0; e < E; ++e) {
     const int32_t s = d->edge_src[e], t = d->edge_dst[e];
     if (s < 0 || s >= V) return fail(MG_ERR_INVALID_ARG, "edge %d: src %d out of range", e, s);
@@ -322,6 +372,9 @@ extern "C" mg_status mg_graph_info(mg_graph g, int32_t* V, int32_t* E, int32_t* 
 extern "C" mg_status mg_graph_slots(mg_graph g, int32_t* vtx_off, int32_t* slot_edge,
                                     uint8_t* slot_end, uint64_t* slot_threshold) {
   if (!g) return fail(MG_ERR_INVALID_ARG, "mg_graph_slots: NULL graph");
+  mg_status s = check_host({{vtx_off, "vtx_off"}, {slot_edge, "slot_edge"}, {slot_end, "slot_end"},
+                            {slot_threshold, "slot_threshold"}});
+  if (s != MG_OK) return s;
   if (vtx_off) memcpy(vtx_off, g->vtx_off.data(), (g->V + 1) * sizeof(int32_t));
   if (slot_edge) memcpy(slot_edge, g->slot_edge.data(), g->S * sizeof(int32_t));
   if (slot_end) memcpy(slot_end, g->slot_end.data(), g->S);
@@ -398,7 +451,10 @@ size_t counter_bytes(const mg_graph g) { return 8 * ((size_t)g->S + g->V + 2) + 
 // in device memory by the init kernel, which sets the device error word).
 mg_status check_positions(mg_particles p, const int32_t* edge0, const double* x0, int on_device) {
   if (!edge0 || !x0) return fail(MG_ERR_INVALID_ARG, "edge0 and x0 are required");
-  if (on_device) return MG_OK;
+  const Mem want = on_device ? Mem::kDevice : Mem::kHost;
+  mg_status s = check_memory(edge0, want, "edge0");
+  if (s == MG_OK) s = check_memory(x0, want, "x0");
+  if (s != MG_OK || on_device) return s;
   const mg_graph g = p->g;
   for (int64_t i = 0; i < p->n; ++i) {
     const int32_t e = edge0[i];
@@ -669,6 +725,7 @@ mg_status check_step_args(double dt, int64_t steps, int32_t M, int32_t hist_bins
   if (M < 1 || M > 1024) return fail(MG_ERR_INVALID_ARG, "max_splits_M must be in [1, 1024]");
   if (hist_bins < 0) return fail(MG_ERR_INVALID_ARG, "hist_bins must be >= 0");
   if (hist_bins > 0 && !hist_out) return fail(MG_ERR_INVALID_ARG, "hist_bins > 0 needs hist_out");
+  if (hist_bins > 0) return check_memory(hist_out, Mem::kDevice, "hist_out");
   return MG_OK;
 }
 
@@ -960,6 +1017,10 @@ extern "C" mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, i
                                   void* stream) {
   if (!p || !out) return fail(MG_ERR_INVALID_ARG, "mg_histogram: NULL argument");
   if (bins < 1) return fail(MG_ERR_INVALID_ARG, "bins must be >= 1");
+  {
+    mg_status s = check_memory(out, out_on_device ? Mem::kDevice : Mem::kHost, "out");
+    if (s != MG_OK) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mg_graph g = p->g;
   const size_t bytes = (size_t)g->E * bins * 4;
@@ -991,6 +1052,11 @@ extern "C" mg_status mg_histogram_binned(mg_particles p, const int32_t* bin_offs
                                          int out_on_device, void* stream) {
   if (!p || !bin_offsets || !out)
     return fail(MG_ERR_INVALID_ARG, "mg_histogram_binned: NULL argument");
+  {
+    mg_status s = check_host({{bin_offsets, "bin_offsets"}, {bin_upper, "bin_upper"}});
+    if (s == MG_OK) s = check_memory(out, out_on_device ? Mem::kDevice : Mem::kHost, "out");
+    if (s != MG_OK) return s;
+  }
   const mg_graph g = p->g;
   if (bin_offsets[0] != 0) return fail(MG_ERR_INVALID_ARG, "bin_offsets[0] must be 0");
   for (int32_t e = 0; e < g->E; ++e)
@@ -1053,6 +1119,11 @@ extern "C" mg_status mg_histogram_binned(mg_particles p, const int32_t* bin_offs
 extern "C" mg_status mg_exit_counts(mg_particles p, uint64_t* slot_exits, uint64_t* absorbed,
                                     uint64_t* truncations, uint64_t* particle_steps, void* stream) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_exit_counts: NULL particles");
+  {
+    mg_status s = check_host({{slot_exits, "slot_exits"}, {absorbed, "absorbed"},
+                              {truncations, "truncations"}, {particle_steps, "particle_steps"}});
+    if (s != MG_OK) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mg_graph g = p->g;
   std::vector<uint64_t> h(counter_bytes(g) / 8 + 1, 0);
@@ -1078,6 +1149,11 @@ extern "C" mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint
                                   uint32_t* hits, uint32_t* first_hits, uint32_t* flags,
                                   uint64_t* step, void* stream) {
   if (!p) return fail(MG_ERR_INVALID_ARG, "mg_state_get: NULL particles");
+  {
+    mg_status s = check_host({{edge, "edge"}, {x, "x"}, {n_draw, "n_draw"}, {hits, "hits"},
+                              {first_hits, "first_hits"}, {flags, "flags"}, {step, "step"}});
+    if (s != MG_OK) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)p->n;
   if (edge) MG_CUDA(cudaMemcpyAsync(edge, p->sv.edge, 4 * n, cudaMemcpyDeviceToHost, st));
@@ -1108,6 +1184,11 @@ extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const dou
                                   uint64_t step, void* stream) {
   if (!p || !edge || !x || !n_draw || !hits || !first_hits || !flags)
     return fail(MG_ERR_INVALID_ARG, "mg_state_set: NULL argument");
+  {
+    mg_status s = check_host({{edge, "edge"}, {x, "x"}, {n_draw, "n_draw"}, {hits, "hits"},
+                              {first_hits, "first_hits"}, {flags, "flags"}});
+    if (s != MG_OK) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)p->n;
   const mg_graph g = p->g;

@@ -73,6 +73,13 @@ extern "C" mg_status mg_histogram_static(mg_particles p, int32_t bins, uint32_t*
   if (!out || !mg_particles_view(p, &g, &edge, &x, &n, &prec))
     return mg_fail_message(MG_ERR_INVALID_ARG, "mg_histogram_static: NULL argument");
   if (bins < 1) return mg_fail_message(MG_ERR_INVALID_ARG, "mg_histogram_static: bins must be >= 1");
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) (void)cudaGetLastError();
+    else if (at.type == cudaMemoryTypeDevice)
+      return mg_fail_message(MG_ERR_INVALID_ARG,
+                             "mg_histogram_static: out must be host memory, not device memory");
+  }
   const int64_t len = (int64_t)g.E * bins;
   if (len > kMaxStaticBins) {
     char msg[256];

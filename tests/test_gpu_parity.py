@@ -453,6 +453,75 @@ def test_device_inputs_and_validation(B):
     g.close()
 
 
+def test_buffers_checked_before_any_launch(B):
+    """Caller buffers the library would read or write out of bounds, or in the
+    wrong memory, are refused before anything runs: by the binding (lengths,
+    dtypes, placement) and, for raw pointers, by the C library (host memory
+    where device memory is required and the reverse).  The set stays usable."""
+    import ctypes as C
+    import torch
+    L = B.load()
+    d = W.random_tree(20, seed=2)
+    g = B.Graph(d)
+    E = g.n_edges
+    e, x = W.uniform_on_edges(d, 1000, 4)
+    with pytest.raises(ValueError):                       # lengths differ
+        B.Particles(g, e[:-1], x, seed=1)
+    with pytest.raises(ValueError):                       # float32 device positions
+        B.Particles(g, torch.from_numpy(e).cuda(), torch.from_numpy(x).float().cuda(), seed=1)
+    with pytest.raises(ValueError):                       # host edges, device positions
+        B.Particles(g, e, torch.from_numpy(x).cuda(), seed=1)
+    p = B.Particles(g, e, x, seed=1, precision=B.MG_FP32_MIXED)
+    with pytest.raises(ValueError):
+        p.reset(e[:10], x[:10])
+    with pytest.raises(ValueError):                       # host histogram for a kernel
+        p.simulate(1e-3, 10, 8, 4, np.zeros(E * 4, np.uint32))
+    with pytest.raises(ValueError):                       # one entry short
+        p.simulate(1e-3, 10, 8, 4, torch.zeros(E * 4 - 1, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        p.simulate(1e-3, 10, 8, 4, torch.zeros(E * 4, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        p.histogram(4, np.zeros(E * 4 - 1, np.uint32))
+    with pytest.raises(ValueError):                       # offsets for fewer edges
+        p.histogram_binned(np.arange(E, dtype=np.int32), np.ones(E - 1))
+    with pytest.raises(ValueError):
+        st = p.state()
+        st["x"] = st["x"][:-1]
+        p.set_state(st)
+    # the C library on raw pointers
+    host = np.zeros(E * 4, np.uint32)
+    assert L.mg_simulate(p.h, 1e-3, 10, 8, 4, C.c_void_p(host.ctypes.data), None) == \
+        B.MG_ERR_INVALID_ARG
+    assert L.mg_histogram(p.h, 4, C.c_void_p(host.ctypes.data), 1, None) == B.MG_ERR_INVALID_ARG
+    dev = torch.zeros(E * 4, dtype=torch.int32, device="cuda")
+    assert L.mg_histogram(p.h, 4, C.c_void_p(dev.data_ptr()), 0, None) == B.MG_ERR_INVALID_ARG
+    assert L.mg_histogram_static(p.h, 4, C.c_void_p(dev.data_ptr()), None) == B.MG_ERR_INVALID_ARG
+    xd = torch.zeros(len(x), dtype=torch.float64, device="cuda")
+    assert L.mg_state_get(p.h, None, C.c_void_p(xd.data_ptr()), None, None, None, None, None,
+                          None) == B.MG_ERR_INVALID_ARG
+    h = C.c_void_p()
+    assert L.mg_particles_init(g.h, len(x), C.c_void_p(e.ctypes.data), C.c_void_p(x.ctypes.data),
+                               1, 0, 1, 0, B.MG_FP32_MIXED, None, C.byref(h)) == \
+        B.MG_ERR_INVALID_ARG
+    s, keep = B._desc_struct(d)
+    src = torch.from_numpy(np.asarray(d["src"], np.int32)).cuda()
+    s.edge_src = C.cast(C.c_void_p(src.data_ptr()), C.POINTER(C.c_int32))
+    assert L.mg_graph_create(C.byref(s), C.byref(h)) == B.MG_ERR_INVALID_ARG
+    assert "device memory" in B.mg_last_error()
+    # nothing ran; the set still works and matches a fresh one
+    p.simulate(1e-3, 10, 8, 4, dev)
+    q = B.Particles(g, e, x, seed=1, precision=B.MG_FP32_MIXED)
+    q.simulate(1e-3, 10, 8)
+    p.synchronize()
+    q.synchronize()
+    sp = p.state()
+    assert np.array_equal(sp["x"], q.state()["x"])
+    assert int(dev.sum()) == int(np.count_nonzero(sp["edge"] >= 0))
+    p.close()
+    q.close()
+    g.close()
+
+
 def test_overflow_to_infinity_is_reported(B):
     """A drift that pushes particles off to infinity on a semi-infinite edge
     (mu = +50 x: x grows by 5% a step) overflows binary32 within ~1800 steps:
