@@ -12,7 +12,10 @@ server's resident graphs.  The server
 * runs rounds on several streams at once, so the work of different rounds
   overlaps on the device;
 * returns a request's histogram and counters when its last round completes,
-  and records arrival, admission and completion times for p50/p99 latency.
+  and records arrival, admission and completion times for p50/p99 latency;
+* fails a single request -- one whose admission or collection raises, e.g.
+  on invalid starting positions or a device error of its own particle set --
+  with its error in the result, and keeps serving the others.
 
 Every particle's draws depend only on (seed, instance = request id, particle
 id) and chunking a run into rounds is bit-exact, so a request's result is the
@@ -54,6 +57,7 @@ class Result:
     admitted: float
     finished: float
     particle_steps: int
+    error: str | None = None  # set when the request failed (then hist is None)
 
     @property
     def latency(self) -> float:
@@ -100,9 +104,15 @@ class Server:
     # ---------------------------------------------------------- one pass
     def step(self) -> list[Result]:
         done = self._complete()
-        self._admit()
+        done += self._admit()
         self._launch()
         return done
+
+    def _failed(self, req: Request, admitted: float, ex: Exception) -> Result:
+        res = Result(req.rid, None, {}, None, req.arrival, admitted, self.clock(), 0,
+                     error=f"{type(ex).__name__}: {ex}")
+        self.results.append(res)
+        return res
 
     def _complete(self) -> list[Result]:
         out = []
@@ -118,28 +128,39 @@ class Server:
                 if act.remaining == 0:
                     keep = (act.req.rid in self.keep_state
                             if isinstance(self.keep_state, (set, frozenset)) else bool(self.keep_state))
-                    hist, counts, state = self.backend.collect(act.handle, keep)
-                    self.backend.release(act.handle)
-                    self.reserved -= self.backend.bytes_of(act.req)
-                    self.active.remove(act)
                     r = act.req
-                    res = Result(r.rid, hist, counts, state, r.arrival, act.admitted, self.clock(),
-                                 int(counts.get("particle_steps", r.n * r.steps)))
-                    self.results.append(res)
-                    out.append(res)
+                    try:
+                        hist, counts, state = self.backend.collect(act.handle, keep)
+                    except Exception as ex:  # this request's failure, not the server's
+                        out.append(self._failed(r, act.admitted, ex))
+                    else:
+                        res = Result(r.rid, hist, counts, state, r.arrival, act.admitted,
+                                     self.clock(), int(counts.get("particle_steps", r.n * r.steps)))
+                        self.results.append(res)
+                        out.append(res)
+                    finally:
+                        self.backend.release(act.handle)
+                        self.reserved -= self.backend.bytes_of(r)
+                        self.active.remove(act)
         return out
 
-    def _admit(self):
+    def _admit(self) -> list[Result]:
+        failed = []
         while self.queue:
             req = self.queue[0]
             need = self.backend.bytes_of(req)
             if self.reserved + need > self.mem_budget:
                 break
             self.queue.popleft()
-            handle = self.backend.admit(req)
+            try:
+                handle = self.backend.admit(req)
+            except Exception as ex:  # e.g. starting positions off their edges
+                failed.append(self._failed(req, self.clock(), ex))
+                continue
             self.reserved += need
             self.peak_reserved = max(self.peak_reserved, self.reserved)
             self.active.append(_Active(req, handle, req.steps, self.clock()))
+        return failed
 
     def _launch(self):
         for k in range(self.n_lanes):
@@ -180,13 +201,20 @@ class Server:
 
 def latency_summary(results: list[Result], t_start: float | None = None,
                     t_end: float | None = None) -> dict:
+    """Latency percentiles and throughput of the requests that succeeded
+    (failed ones are counted apart)."""
+    failed = sum(1 for r in results if r.error is not None)
+    results = [r for r in results if r.error is None]
+    if not results:
+        return dict(requests=0, failed=failed, p50_s=None, p99_s=None, mean_s=None,
+                    particle_steps=0, served_particle_steps_per_s=0.0)
     lat = np.array([r.latency for r in results])
     ps = sum(r.particle_steps for r in results)
     if t_start is None:
         t_start = min(r.arrival for r in results)
     if t_end is None:
         t_end = max(r.finished for r in results)
-    return dict(requests=len(results), p50_s=float(np.percentile(lat, 50)),
+    return dict(requests=len(results), failed=failed, p50_s=float(np.percentile(lat, 50)),
                 p99_s=float(np.percentile(lat, 99)), mean_s=float(lat.mean()),
                 particle_steps=int(ps), served_particle_steps_per_s=ps / max(t_end - t_start, 1e-9))
 

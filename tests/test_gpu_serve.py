@@ -51,6 +51,55 @@ def test_served_equals_alone(prec):
     be.close()
 
 
+def test_failed_request_is_isolated():
+    """One request with a starting position off its edge (refused at
+    admission) and one whose drift carries its particles off to infinity on a
+    semi-infinite edge (a device error of its own set, found at collection)
+    fail alone: their results carry the error, every other request completes
+    and equals its run alone."""
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    graphs = {"star3": W.star_brownian(3),
+              "runaway": dict(W.paper_star("quadratic", k=2), c1=np.array([50.0, -10.0]))}
+    reqs = []
+    for i in range(8):
+        key = "runaway" if i == 5 else "star3"
+        n = 256 + 64 * i
+        if key == "runaway":
+            e0, x0 = np.zeros(n, np.int32), np.full(n, 1.0)
+            steps = 4000
+        else:
+            e0, x0 = W.uniform_on_edges(graphs[key], n, 50 + i)
+            steps = 300
+        if i == 2:
+            x0 = x0.copy()
+            x0[7] = 1.5  # the edges have length 1
+        reqs.append(serve.Request(i, key, n, steps, 1e-3, 8, 16, e0, x0, 0.001 * i))
+    be = serve.GpuBackend(graphs, B.MG_FP32_MIXED, seed=7, n_lanes=2)
+    srv = serve.Server(be, mem_budget=1 << 30, n_lanes=2, chunk_steps=100, keep_state=True)
+    res = srv.run_trace(reqs, time_limit=300)
+    by = {r.rid: r for r in res}
+    assert sorted(by) == list(range(8)) and srv.reserved == 0
+    assert by[2].error and "INVALID_ARG" in by[2].error
+    assert by[5].error and "DEVICE_FAULT" in by[5].error
+    G = {k: B.Graph(d) for k, d in graphs.items()}
+    for q in reqs:
+        if q.rid in (2, 5):
+            continue
+        assert by[q.rid].error is None
+        p = B.Particles(G[q.graph], q.edge0, q.x0, seed=7, instance=q.rid,
+                        precision=B.MG_FP32_MIXED)
+        p.simulate(q.dt, q.steps, q.M)
+        st = p.state()
+        p.close()
+        assert np.array_equal(st["x"], by[q.rid].state["x"])
+        assert np.array_equal(st["edge"], by[q.rid].state["edge"])
+    s = serve.latency_summary(res)
+    assert s["requests"] == 6 and s["failed"] == 2
+    be.close()
+    for g in G.values():
+        g.close()
+
 def test_plain_path_runs():
     graphs = _graphs()
     reqs = serve.poisson_trace(200.0, 0.03, 5, graphs, n_range=(8, 10), steps_range=(10, 50),

@@ -134,3 +134,53 @@ def test_poisson_trace_shape():
     assert np.all(np.diff(arr) > 0) and arr[-1] <= 5.0
     assert all(2 ** 14 - 1 <= q.n <= 2 ** 24 + 1 for q in tr)
     assert all(100 <= q.steps <= 5000 for q in tr)
+
+
+class FailingBackend(FakeBackend):
+    """Admission of some requests raises (invalid input), collection of
+    others raises (a device error of their own particle set)."""
+
+    def __init__(self, bad_admit, bad_collect):
+        super().__init__()
+        self.bad_admit, self.bad_collect = set(bad_admit), set(bad_collect)
+        self.released = []
+
+    def admit(self, req):
+        if req.rid in self.bad_admit:
+            raise ValueError(f"request {req.rid}: starting position off its edge")
+        return super().admit(req)
+
+    def collect(self, rid, keep_state):
+        if rid in self.bad_collect:
+            raise RuntimeError(f"request {rid}: device error bits 0x2")
+        return super().collect(rid, keep_state)
+
+    def release(self, rid):
+        self.released.append(rid)
+        super().release(rid)
+
+
+def test_failed_request_does_not_stop_the_others():
+    be = FailingBackend(bad_admit=[3, 17], bad_collect=[5, 30])
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=60_000, n_lanes=2, chunk_steps=500, clock=clk)
+    reqs = _reqs(40, seed=4)
+    for q in reqs:
+        srv.submit(q)
+    for _ in range(100_000):
+        if srv.idle():
+            break
+        srv.step()
+        clk.t += 1.0
+    assert srv.idle() and srv.reserved == 0 and not be.live
+    by = {r.rid: r for r in srv.results}
+    assert sorted(by) == list(range(40))          # every request answered once
+    for rid in (3, 17, 5, 30):
+        assert by[rid].error and by[rid].hist is None
+    assert "off its edge" in by[3].error and "device error" in by[5].error
+    assert 3 not in be.released and 5 in be.released   # admitted sets are freed
+    for q in reqs:
+        if q.rid not in (3, 17, 5, 30):
+            assert by[q.rid].error is None and be.steps_done[q.rid] == q.steps
+    s = serve.latency_summary(srv.results)
+    assert s["requests"] == 36 and s["failed"] == 4
