@@ -63,7 +63,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
     procs, objs = [], []
     for src, extra in UNITS:
-        obj = os.path.join(BUILD, src.rsplit(".", 1)[0] + ".o")
+        # per-process object names: concurrent builds (test workers) do not
+        # overwrite each other's objects; the library is replaced atomically
+        obj = os.path.join(BUILD, f"{src.rsplit('.', 1)[0]}.{os.getpid()}.o")
         cmd = [nvcc, *ARCH, *common, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]
@@ -83,6 +85,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout.decode(errors='replace')}")
     os.replace(tmp, LIB)
+    for obj in objs:
+        try:
+            os.remove(obj)
+        except OSError:
+            pass
     if verbose or ptxas_info:
         print("\n".join(logs), file=sys.stderr)
     return LIB
