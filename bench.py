@@ -17,6 +17,8 @@ mg_simulate, the histogram and the counters read back to the host.
 ``--impl reference`` times the plain CPU oracle on the host cores instead.
 Under torchrun each rank simulates its own N particles (ids rank*N ..), so
 the scaling is weak; there is no collective on the data path.
+``--workload`` runs the other configurations instead (the 3-edge Brownian
+star, the vascular network, the 512-instance batch, the served trace).
 """
 from __future__ import annotations
 
@@ -54,7 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default=None,
+                    help="default: mixed (star3_brownian: fp64, as that configuration is given)")
     ap.add_argument("--split-batch", type=int, default=0)
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--em-steps", type=int, default=EM_STEPS)
@@ -66,10 +69,15 @@ def parse():
                     help="batch512: scale every instance's particle count by this factor")
     ap.add_argument("--cpu-sample", type=int, default=16_384)
     ap.add_argument("--workload", default="star16_langevin",
-                    choices=["star16_langevin", "vascular", "batch512", "served"],
+                    choices=["star16_langevin", "star3_brownian", "vascular", "batch512",
+                             "served"],
                     help="star16_langevin is the headline; the others report the "
                          "vascular, batched and served configurations")
-    return ap.parse_args()
+    args = ap.parse_args()
+    args.precision_given = args.precision is not None
+    if args.precision is None:
+        args.precision = "mixed"
+    return args
 
 
 def config(args, world):
@@ -431,6 +439,64 @@ def run_vascular(args):
     return 0
 
 
+def run_star3(args):
+    """The small star: 3 edges of length 1, standard Brownian motion, 10^4
+    particles round-robin on the edges, dt = 1e-3, 1000 EM-Steps, M = 8,
+    32-bin histograms and the exit counts; FP64 unless --precision says
+    otherwise.  Each benchmark step restarts from the device-resident start.
+    40 blocks of 256 particles cannot fill 152 SMs: the number shows what a
+    single small launch costs, not the kernel's throughput."""
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    d = W.star_brownian(3)
+    n = 10_000 if args.n == (1 << 24) else args.n
+    steps = 1000 if args.em_steps == EM_STEPS else args.em_steps
+    M3, bins = 8, 32
+    prec = args.precision if args.precision_given else "fp64"
+    e0, x0 = W.round_robin_uniform(d, n, 0)
+    B.load()
+    B.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    g = B.Graph(d)
+    de, dx = torch.from_numpy(e0).cuda(), torch.from_numpy(x0).cuda()
+    p = B.Particles(g, de, dx, seed=0, precision=_mode(B, prec), stream=stream)
+    hist = torch.zeros(g.n_edges * bins, dtype=torch.int32, device="cuda")
+
+    def step():
+        p.reset(de, dx, stream)
+        hist.zero_()
+        p.simulate(1e-3, steps, M3, bins, hist, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    ev = _events(torch, args.steps)
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    c = p.counts(stream)
+    ps = c["particle_steps"] * args.steps  # counters restart with every reset
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    out = {"metric": METRIC, "value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+           "data": "synthetic",
+           "config": {"workload": "star3_brownian", "edges": 3, "n_particles": n, "dt": 1e-3,
+                      "em_steps_per_step": steps, "M": M3, "hist_bins_per_edge": bins,
+                      "precision": prec, "blocks": (n + 255) // 256,
+                      "l2": "state below L2; each step restarts from the same start"},
+           "centre_exits": [int(v) for v in c["exits"][:3]], "launch_ms": ms}
+    p.close()
+    g.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_batch512(args):
     """512 uneven instances (stars with 3..64 edges, random trees with
     100..10^4 edges, N ~ 2^U[12,22], 100..5000 steps) in one persistent launch,
@@ -551,6 +617,8 @@ def main():
         return run_reference(args)
     if args.workload == "vascular":
         return run_vascular(args)
+    if args.workload == "star3_brownian":
+        return run_star3(args)
     if args.workload == "batch512":
         return run_batch512(args)
     if args.workload == "served":

@@ -37,6 +37,23 @@ cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_
   return cudaGetLastError();
 }
 
+int em_step_blocks_per_sm_f32x(int mode, size_t smem) {
+  int nb = 0;
+  if (mode == kModeMixed) {
+    set_smem_attributes<kModeMixed>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeMixed>, kBlock, smem);
+  } else {
+    set_smem_attributes<kModeF32>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeF32>, kBlock, smem);
+  }
+  return nb;
+}
+
+int em_step_blocks_per_sm(int mode, size_t smem) {
+  return mode == kModeF64 ? em_step_blocks_per_sm_f64(smem)
+                          : em_step_blocks_per_sm_f32x(mode, smem);
+}
+
 int em_range_blocks_per_sm_f32x(int mode, size_t smem) {
   int nb = 0;
   if (mode == kModeMixed) {

@@ -29,6 +29,13 @@ cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cud
   return cudaGetLastError();
 }
 
+int em_step_blocks_per_sm_f64(size_t smem) {
+  set_smem_attributes();
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeF64>, kBlock, smem);
+  return nb;
+}
+
 int em_range_blocks_per_sm_f64(size_t smem) {
   set_smem_attributes();
   int nb = 0;

@@ -1135,12 +1135,16 @@ __global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
 }
 
 // The fused EM-Step kernel over one particle set: block b takes particles
-// b * 256 .. b * 256 + 255.
+// b * r .. b * r + r - 1, r = a.range (256, or fewer for a set too small to
+// fill the GPU's resident blocks).
 template <int kMode>
 __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ SimArgs a,
                                                       const __grid_constant__ Keys keys) {
   extern __shared__ __align__(16) unsigned char smem[];
-  run_tile<kMode>(a, keys, (int64_t)blockIdx.x * kThreads + threadIdx.x, smem);
+  // a.range <= 256 particles per block; the block's other threads are idle
+  const int64_t i =
+      (threadIdx.x < a.range) ? (int64_t)blockIdx.x * a.range + threadIdx.x : a.n;
+  run_tile<kMode>(a, keys, i, smem);
 }
 
 // The batched, persistent form: each block pops work items -- 256 particles

@@ -16,8 +16,12 @@ cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cud
 cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
                                 cudaStream_t st);
 // (a.range > 256 launches the range kernel: lanes claim particles of their
-// block's range.)  Resident blocks per SM of the range kernel at `smem` bytes
-// of dynamic shared memory.
+// block's range; a.range <= 256 the tile kernel, a.range particles per
+// block.)  Resident blocks per SM of either kernel at `smem` bytes of dynamic
+// shared memory.
+int em_step_blocks_per_sm(int mode, size_t smem);
+int em_step_blocks_per_sm_f64(size_t smem);
+int em_step_blocks_per_sm_f32x(int mode, size_t smem);
 int em_range_blocks_per_sm(int mode, size_t smem);
 int em_range_blocks_per_sm_f64(size_t smem);
 int em_range_blocks_per_sm_f32x(int mode, size_t smem);

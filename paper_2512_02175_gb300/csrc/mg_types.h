@@ -105,7 +105,7 @@ struct SimArgs {
   int32_t stage_smem;   // graph tables staged in shared memory
   int32_t smem_counters;// exit/absorbed counters privatised in shared memory
   int32_t smem_hist;    // histogram privatised in shared memory
-  int64_t range;        // particles per block of the range kernel
+  int64_t range;        // particles per block: <= 256 em_step_kernel, > 256 the range kernel
 };
 
 // Dynamic shared memory of the fused kernel: staged tables, privatised

@@ -376,6 +376,35 @@ def test_particles_per_block_do_not_change_results(B, prec):
         assert np.array_equal(ref_hist, hist)
 
 
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_small_set_spread_over_more_blocks(B, prec):
+    """A set too small to fill the GPU runs with fewer particles per block
+    (down to 32; the rest of each block idles): every particle's trajectory
+    and the counters are bit for bit those of the same particles inside a
+    large set, which runs 256 per block."""
+    import torch
+    d = W.star_langevin(16)
+    n_big, n_small = 1 << 19, 5000
+    e, x = W.uniform_on_edges(d, n_big, 6)
+    g = B.Graph(d)
+    runs = []
+    for n in (n_small, n_big, 33, 1):
+        p = B.Particles(g, e[:n], x[:n], seed=2, precision=MODES[prec])
+        h = torch.zeros(g.n_edges * 4, dtype=torch.int32, device="cuda")
+        p.simulate(1e-3, 120, 16, 4, h)
+        p.synchronize()
+        runs.append((p.state(), p.counts(), h.cpu().numpy()))
+        p.close()
+    g.close()
+    small, big = runs[0][0], runs[1][0]
+    for k in ("edge", "x", "n_draw", "hits", "first_hits", "flags"):
+        assert np.array_equal(small[k], big[k][:n_small]), k
+        assert np.array_equal(runs[2][0][k], big[k][:33]), k
+        assert np.array_equal(runs[3][0][k], big[k][:1]), k
+    assert runs[0][1]["particle_steps"] == n_small * 120
+    assert runs[0][2].sum() == n_small and runs[2][2].sum() == 33
+
 def test_fused_histogram_matches_standalone(B):
     import torch
     d = W.star_langevin(16)
