@@ -710,18 +710,21 @@ int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
-  if (!p->g->has_absorbing || (p->max_blocks == 0 && steps_per_launch < kRangeMinSteps)) {
+  if (p->max_blocks == 0) {
     // one particle per thread; a set smaller than the resident blocks x 256
     // is spread over more blocks of fewer particles (a multiple of 32, at
     // least 32; the other threads idle), so that every SM gets work: the
     // warps are latency-bound, and one SM running eight of them is slower
     // than four SMs running two each
-    int per_sm = mg::em_step_blocks_per_sm((int)p->prec, smem);
+    const int per_sm = mg::em_step_blocks_per_sm((int)p->prec, smem);
     const int64_t slots = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
-    if (tiles >= slots) return mg::kBlock;
-    const int64_t want = (p->n + slots - 1) / slots;
-    return std::min<int64_t>(mg::kBlock, std::max<int64_t>(32, (want + 31) / 32 * 32));
+    if (tiles < slots) {
+      const int64_t want = (p->n + slots - 1) / slots;
+      return std::min<int64_t>(mg::kBlock, std::max<int64_t>(32, (want + 31) / 32 * 32));
+    }
   }
+  if (!p->g->has_absorbing || (p->max_blocks == 0 && steps_per_launch < kRangeMinSteps))
+    return mg::kBlock;
   const int per_sm = mg::em_range_blocks_per_sm((int)p->prec, smem);
   int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   if (p->max_blocks > 0 && p->max_blocks < blocks) blocks = p->max_blocks;

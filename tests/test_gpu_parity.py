@@ -6,7 +6,8 @@ Tolerances:
   1e-12 max(1, |x|); particles whose trajectory passed within 1e-9 of a
   branch (flag bit 0 on either side) are excluded, and counted.  The only
   allowed differences are the ulp-level results of log / sin / cos on the two
-  sides, which a 1e-9 branch margin cannot turn into a different decision.
+  sides (test_fp64_normals_match_oracle), which a 1e-9 branch margin cannot
+  turn into a different decision.
 * FP32-mixed mode: statistical -- per-edge occupancy and per-slot exit
   frequencies within 3 standard errors of the oracle's (same Philox streams),
   coupled final-edge agreement, and the histogram total-variation distance.
@@ -114,6 +115,32 @@ def test_star3_fp64_matches_golden_values(B):
     assert cn["exits"].tolist() == gold["exits"]
     assert cn["particle_steps"] == gold["particle_steps"]
 
+
+
+def test_fp64_normals_match_oracle(B):
+    """The binary64 mode's normals against the oracle's (both Box-Muller in
+    binary64, CUDA's and the host's libm): four drift-free steps of length h
+    from x0 = 1/2 on long edges move a particle by
+    sigma sqrt(h) (z0 + z1 + z2 + z3), so the position difference bounds the
+    normals' difference.  262 144 particles, 2^20 normals covering all four
+    words of a Philox block: every position within 1e-15, i.e. the normals
+    agree to a few ulps -- the accuracy the 1e-12 trajectory bound needs, as
+    a near-grazing split (time left a few 1e-9 dt) amplifies a normal's
+    error by up to ~1e4.  The largest difference is printed."""
+    d = W.star_brownian(3, length=1000.0)  # mu = 0, sigma = 1
+    n, dt, steps = 1 << 18, 2.5e-3, 4
+    e = (np.arange(n) % 3).astype(np.int32)
+    x = np.full(n, 0.5)
+    gs, gc, _ = gpu_run(B, d, e, x, seed=9, dt=dt, steps=steps, M=8, prec=B.MG_FP64)
+    o = oracle_pool.run(d, e, x, seed=9, dt=dt, steps=steps, M=8)
+    ok = (gs["hits"] == 0) & (o["hits"] == 0)
+    assert ok.mean() > 0.999
+    assert np.array_equal(gs["n_draw"], o["n_draw"]) and int(gs["n_draw"][0]) == steps
+    dx = np.abs(gs["x"][ok] - o["x"][ok])
+    disp = np.abs(o["x"][ok] - 0.5).max()
+    print(f"\nmax |x_gpu - x_oracle| after {steps} steps: {dx.max():.2e} "
+          f"(largest displacement {disp:.3f})")
+    assert dx.max() <= 1e-15
 
 def test_mixed_graph_fp64_unaligned_chunks(B):
     """Cycles, a self-loop, a semi-infinite edge, zero weights, absorbing
