@@ -199,13 +199,15 @@ def run_reference(args):
 # --------------------------------------------------------------- our path
 
 PROFILE_KEYS = ("kernel-sha256", "dram-bytes-per-launch-full-size", "issue-active-pct",
-                "warp-inst-per-warp-step")
+                "warp-inst-per-warp-step", "fp64-pipe-active-pct")
+PROFILE_N = 1 << 24  # particles of the launch the summaries' traffic is scaled to
 
 
-def _profile(kernel_hash):
-    """Figures of the committed ncu summary of the fused kernel, if it was
-    taken on the current kernel source (else an empty dict)."""
-    path = os.path.join(ROOT, "profiles", "em_step_star16_langevin.md")
+def _profile(kernel_hash, name="em_step_star16_langevin.md"):
+    """Figures of a committed ncu summary of the fused kernel (the FP32-mixed
+    one by default), if it was taken on the current kernel source (else an
+    empty dict)."""
+    path = os.path.join(ROOT, "profiles", name)
     rec = {}
     try:
         with open(path) as f:
@@ -218,10 +220,11 @@ def _profile(kernel_hash):
     return rec if rec.get("kernel-sha256") == kernel_hash else {}
 
 
-def _traffic(kernel_hash):
-    """DRAM bytes per launch from the committed ncu summary, or null."""
-    v = _profile(kernel_hash).get("dram-bytes-per-launch-full-size")
-    return int(v) if v else None
+def _traffic(prof, n):
+    """DRAM bytes per launch of n particles from an ncu summary (state
+    traffic is per particle per launch), or null."""
+    v = prof.get("dram-bytes-per-launch-full-size")
+    return int(int(v) * n / PROFILE_N) if v else None
 
 
 def kernel_hash():
@@ -309,15 +312,28 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
-    prof = _profile(kernel_hash())
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                "frac": achieved / peak, "traffic": _traffic(kernel_hash()),
-                "note": f"{I_ALG} algorithmic thread-instructions per particle-step (fast path) x "
-                        f"particle-steps per launch / mean launch time; peak = "
-                        f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"}
-    if prof:  # the issue-rate view, from the committed ncu capture of this kernel
-        roofline["issue_active_frac"] = float(prof["issue-active-pct"]) / 100.0
-        roofline["warp_inst_per_warp_step"] = float(prof["warp-inst-per-warp-step"])
+    if args.precision == "fp64":
+        # bound by the binary64 pipe: its busy fraction in the committed ncu
+        # capture of the binary64 kernel (while that matches the source)
+        prof = _profile(kernel_hash(), "em_step_star16_fp64.md")
+        phi = float(prof["fp64-pipe-active-pct"]) / 100.0 if prof else None
+        roofline = {"bound": "fp64", "achieved": phi, "peak": 1.0 if prof else None,
+                    "unit": "FP64-pipe busy fraction", "frac": phi,
+                    "traffic": _traffic(prof, n),
+                    "note": "binary64 pipe cycles active / peak (ncu, "
+                            "profiles/em_step_star16_fp64.md); the binary64 mode is "
+                            "bound by GB300's binary64 rate"}
+    else:
+        # the summary's figures describe the FP32-mixed kernel
+        prof = _profile(kernel_hash()) if args.precision == "mixed" else {}
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+                    "frac": achieved / peak, "traffic": _traffic(prof, n),
+                    "note": f"{I_ALG} algorithmic thread-instructions per particle-step (fast "
+                            f"path) x particle-steps per launch / mean launch time; peak = "
+                            f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"}
+        if prof:  # the issue-rate view, from the committed ncu capture of this kernel
+            roofline["issue_active_frac"] = float(prof["issue-active-pct"]) / 100.0
+            roofline["warp_inst_per_warp_step"] = float(prof["warp-inst-per-warp-step"])
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
