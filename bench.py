@@ -228,12 +228,12 @@ def _traffic(prof, n):
 
 
 def kernel_hash():
-    """sha256 of the sources that define the fused EM-Step kernel (its body
-    and its table layouts): a committed ncu figure counts only while these
-    are unchanged."""
+    """sha256 of the sources that define the fused EM-Step kernel (its body,
+    its table layouts and the logarithm table of the binary64 mode): a
+    committed ncu figure counts only while these are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2512_02175_gb300", "csrc")
-    for f in ("mg_em_step.cuh", "mg_types.h"):
+    for f in ("mg_em_step.cuh", "mg_types.h", "mg_log_table.h"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

