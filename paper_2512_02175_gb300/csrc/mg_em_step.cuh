@@ -518,10 +518,27 @@ __device__ __forceinline__ typename Types<kMode>::R sub_step_end(const Lane<kMod
   }
 }
 
+// Comparisons of binary64 numbers on their bit patterns, for numbers that
+// are not NaN: a non-negative binary64 number orders as its bits read as a
+// signed 64-bit integer, a negative one reads negative.  Exactly the
+// floating-point comparisons, on the integer pipes instead of GB300's slow
+// binary64 pipe.  abs_below(v, b): |v| < b for b >= 0.
+__device__ __forceinline__ bool abs_below(double v, double b) {
+  return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) < __double_as_longlong(b);
+}
+
+// x~ in (0, l_e) for binary64, l_e > 0 (+inf on a semi-infinite edge)
+__device__ __forceinline__ bool inside(double xt, double L) {
+  const long long b = __double_as_longlong(xt);
+  return (b > 0) & (b < __double_as_longlong(L));
+}
+
 template <int kMode>
 __device__ __forceinline__ void mark_near_branch(Lane<kMode>& p, typename Types<kMode>::R xt) {
   if constexpr (kMode == kModeF64) {
-    if (fabs(xt) < p.tol || (isfinite(p.L) && fabs(p.L - xt) < p.tol)) p.flags |= 1u;
+    const bool finite_L =  // l_e < +inf, from its exponent bits
+        (__double_as_longlong(p.L) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
+    if (abs_below(xt, p.tol) || (finite_L && abs_below(p.L - xt, p.tol))) p.flags |= 1u;
   }
 }
 
@@ -536,7 +553,10 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
   p.n_draw++;
   const R xt = sub_step_end(p, apply_sign(z, p.wand, p.wor));
   mark_near_branch(p, xt);
-  if (xt > R(0) && xt < p.L) {
+  bool in;
+  if constexpr (kMode == kModeF64) in = inside(xt, p.L);
+  else in = xt > R(0) && xt < p.L;
+  if (in) {
     count_exit(a.c, bc, p.cur_slot);
     if (p.in_cont) use_step_coefficients(p, a);
     p.k = 0;
@@ -585,7 +605,9 @@ __device__ __forceinline__ void interior_sub_steps(Lane<kMode>& p, const typenam
       xt = fmaf(xc, p.Qm, fmaf(p.Sm, z, p.Pm));
       xc = xt;
     }
-    const bool in = att & (xt > R(0)) & (xt < p.L);
+    bool in;
+    if constexpr (kMode == kModeF64) in = att & inside(xt, p.L);
+    else in = att & (xt > R(0)) & (xt < p.L);
     p.x = in ? xt : p.x;
     n_in += in ? 1u : 0u;
     go = in;
