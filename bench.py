@@ -591,9 +591,9 @@ def run_served(args):
     """A Poisson request stream (200 requests/s over 3 s) over the 3-edge
     Brownian star, the 16-edge Langevin star and the vascular network; n =
     2^U[12,18], steps log-U[100, 5000], dt log-U[1e-4, 1e-2].  The continuous-
-    batching server (binary32-mixed, 2 streams, rounds of 500 steps, 32 GB
-    admission budget) against the plain path: each request alone as one FP64
-    mg_simulate, in arrival order."""
+    batching server (binary32-mixed, 2 streams, rounds of max(500 steps,
+    2^27 particle-steps) per member, 32 GB admission budget) against the plain
+    path: each request alone as one FP64 mg_simulate, in arrival order."""
     import torch
     from paper_2512_02175_gb300 import binding as B
     from paper_2512_02175_gb300 import serve
@@ -604,7 +604,7 @@ def run_served(args):
     trace = lambda: serve.poisson_trace(200.0, 3.0, 17, graphs, n_range=(12, 18),
                                          init=serve.default_init)
     be = serve.GpuBackend(graphs, _mode(B, args.precision), seed=SEED, n_lanes=2)
-    srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500)
+    srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500, round_work=1 << 27)
     # warm-up: a short trace (allocator, module load, graph capture paths)
     warm = serve.poisson_trace(200.0, 0.2, 99, graphs, n_range=(10, 12), init=serve.default_init)
     srv.run_trace(warm)
@@ -621,7 +621,7 @@ def run_served(args):
            "config": {"workload": "served", "rate_per_s": 200, "window_s": 3.0,
                       "n_range_log2": [12, 18], "steps_range": [100, 5000],
                       "dt_range": [1e-4, 1e-2], "precision": args.precision,
-                      "lanes": 2, "chunk_steps": 500},
+                      "lanes": 2, "chunk_steps": 500, "round_work": 1 << 27},
            "served": served, "plain_fp64_per_request": plain}
     print(json.dumps(out))
     return 0

@@ -7,8 +7,10 @@ server's resident graphs.  The server
   and histogram) fits a budget; later ones wait;
 * keeps admitted requests resident and advances them in rounds: each round is
   one batched launch (``mg_batch``) over the admitted requests that are not
-  already in flight, each taking at most ``chunk_steps`` of its remaining
-  steps, so requests that arrive while others run join at the next round;
+  already in flight, each taking the next part of its remaining steps --
+  ``chunk_steps``, or more for a small request, up to ``round_work``
+  particle-steps -- so requests that arrive while others run join at the
+  next round, and a small request is done in one round;
 * runs rounds on several streams at once, so the work of different rounds
   overlaps on the device;
 * returns a request's histogram and counters when its last round completes,
@@ -75,13 +77,17 @@ class _Active:
 
 class Server:
     def __init__(self, backend, mem_budget: int, n_lanes: int = 2, chunk_steps: int = 500,
-                 max_members: int = 512, clock=time.perf_counter, keep_state=False):
+                 max_members: int = 512, clock=time.perf_counter, keep_state=False,
+                 round_work: int = 0):
         """keep_state: return every request's final particle state (True), none
-        (False), or those of the request ids in a given set."""
+        (False), or those of the request ids in a given set.  A member takes
+        max(chunk_steps, round_work // n) of its remaining steps per round
+        (round_work = 0: chunk_steps)."""
         self.backend = backend
         self.mem_budget = int(mem_budget)
         self.n_lanes = n_lanes
         self.chunk_steps = int(chunk_steps)
+        self.round_work = int(round_work)
         self.max_members = max_members
         self.clock = clock
         self.keep_state = keep_state
@@ -171,7 +177,8 @@ class Server:
                 return
             members = []
             for a in ready[: self.max_members]:
-                now = min(self.chunk_steps, a.remaining)
+                quota = max(self.chunk_steps, self.round_work // max(1, a.req.n))
+                now = min(quota, a.remaining)
                 a.remaining -= now
                 a.in_flight = True
                 members.append((a, now))

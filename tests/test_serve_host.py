@@ -184,3 +184,30 @@ def test_failed_request_does_not_stop_the_others():
             assert by[q.rid].error is None and be.steps_done[q.rid] == q.steps
     s = serve.latency_summary(srv.results)
     assert s["requests"] == 36 and s["failed"] == 4
+
+
+def test_rounds_sized_by_work():
+    """With round_work, a member takes max(chunk_steps, round_work // n)
+    of its remaining steps per round: a small request is done in one round, a
+    large one in several, and every request still gets all its steps."""
+    be = FakeBackend(delay_polls=1)
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=10**9, n_lanes=2, chunk_steps=100, clock=clk,
+                       round_work=1_000_000)
+    small = serve.Request(0, "g", 1000, 900, 1e-3)      # quota 1000 steps: one round
+    large = serve.Request(1, "g", 100_000, 900, 1e-3)   # quota 100 steps: nine rounds
+    for q in (small, large):
+        srv.submit(q)
+    for _ in range(10_000):
+        if srv.idle():
+            break
+        srv.step()
+        clk.t += 1.0
+    assert srv.idle()
+    rounds = {0: [], 1: []}
+    for tok in be.launches:
+        for rid, s in tok["members"]:
+            rounds[rid].append(s)
+    assert rounds[0] == [900]
+    assert rounds[1] == [100] * 9
+    assert be.steps_done == {0: 900, 1: 900}
