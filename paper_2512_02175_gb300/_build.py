@@ -28,7 +28,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("em_step_f32.cu", []),
     ("em_step_f64.cu", ["--fmad=false"]),
-    ("mg_api.cpp", ["-Xcompiler", "-ffp-contract=off"]),
+    ("mg_api.cpp", ["-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-pthread"]),
     ("mg_noalloc.cu", []),
 ]
 
@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         if pr.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{out.decode(errors='replace')}")
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout.decode(errors='replace')}")
