@@ -91,6 +91,48 @@ mg_status check_host(std::initializer_list<std::pair<const void*, const char*>> 
   return MG_OK;
 }
 
+// Pinned host memory of the calling thread for results copied to the host
+// (grown as needed, up to kStageMax, and kept for the thread's life): a copy
+// into it runs at DMA speed, one into ordinary host memory goes through the
+// driver's own staging, several times slower for megabytes (a vascular
+// graph's histogram and counters).  Null if pinned memory cannot be had.
+constexpr size_t kStageMax = 64u << 20;
+
+struct PinnedStage {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinnedStage() {
+    if (p) (void)cudaFreeHost(p);  // may run after the runtime has unloaded
+  }
+  void* get(size_t n) {
+    if (n > kStageMax) return nullptr;
+    if (n > bytes) {
+      if (p) (void)cudaFreeHost(p);
+      p = nullptr;
+      bytes = 0;
+      const size_t want = std::max(n, (size_t)1 << 20);
+      if (cudaMallocHost(&p, want) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p = nullptr;
+        return nullptr;
+      }
+      bytes = want;
+    }
+    return p;
+  }
+};
+thread_local PinnedStage g_stage;
+
+// Device-to-host copy of `bytes` through the pinned stage (then a host
+// copy), or straight into dst; returns after the copy has completed.
+cudaError_t copy_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  void* stage = g_stage.get(bytes);
+  cudaError_t e = cudaMemcpyAsync(stage ? stage : dst, src, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && stage) memcpy(dst, stage, bytes);
+  return e;
+}
+
 // ---------------------------------------------------------------- memory
 
 std::mutex g_alloc_mu;
@@ -1093,10 +1135,7 @@ extern "C" mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, i
                        : mg::launch_histogram_f32(g->view, p->sv.edge, p->sv.x, p->n, bins, dst, sm, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "mg_histogram: launch");
   p->last_stream = st;
-  if (!out_on_device) {
-    MG_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
-    MG_CUDA(cudaStreamSynchronize(st));
-  }
+  if (!out_on_device) MG_CUDA(copy_to_host(out, dst, bytes, st));
   return MG_OK;
 }
 
@@ -1179,12 +1218,17 @@ extern "C" mg_status mg_exit_counts(mg_particles p, uint64_t* slot_exits, uint64
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mg_graph g = p->g;
-  std::vector<uint64_t> h(counter_bytes(g) / 8 + 1, 0);
-  MG_CUDA(cudaMemcpyAsync(h.data(), p->counters.p, 8 * ((size_t)g->S + g->V + 2),
-                          cudaMemcpyDeviceToHost, st));
+  const size_t nw = (size_t)g->S + g->V + 2;
+  std::vector<uint64_t> fallback;
+  uint64_t* h = static_cast<uint64_t*>(g_stage.get(8 * nw));  // pinned, else ordinary
+  if (!h) {
+    fallback.resize(nw);
+    h = fallback.data();
+  }
+  MG_CUDA(cudaMemcpyAsync(h, p->counters.p, 8 * nw, cudaMemcpyDeviceToHost, st));
   MG_CUDA(cudaStreamSynchronize(st));
-  if (slot_exits) memcpy(slot_exits, h.data(), 8 * (size_t)g->S);
-  if (absorbed) memcpy(absorbed, h.data() + g->S, 8 * (size_t)g->V);
+  if (slot_exits) memcpy(slot_exits, h, 8 * (size_t)g->S);
+  if (absorbed) memcpy(absorbed, h + g->S, 8 * (size_t)g->V);
   if (truncations) *truncations = h[g->S + g->V];
   if (particle_steps) *particle_steps = h[g->S + g->V + 1];
   return MG_OK;
