@@ -132,23 +132,27 @@ class Server:
             for act, _ in members:
                 act.in_flight = False
                 if act.remaining == 0:
-                    keep = (act.req.rid in self.keep_state
-                            if isinstance(self.keep_state, (set, frozenset)) else bool(self.keep_state))
-                    r = act.req
-                    try:
-                        hist, counts, state = self.backend.collect(act.handle, keep)
-                    except Exception as ex:  # this request's failure, not the server's
-                        out.append(self._failed(r, act.admitted, ex))
-                    else:
-                        res = Result(r.rid, hist, counts, state, r.arrival, act.admitted,
-                                     self.clock(), int(counts.get("particle_steps", r.n * r.steps)))
-                        self.results.append(res)
-                        out.append(res)
-                    finally:
-                        self.backend.release(act.handle)
-                        self.reserved -= self.backend.bytes_of(r)
-                        self.active.remove(act)
+                    out.extend(self._finish(act))
         return out
+
+    def _finish(self, act: _Active) -> list[Result]:
+        """Collect a request whose steps are all done, and release it."""
+        keep = (act.req.rid in self.keep_state
+                if isinstance(self.keep_state, (set, frozenset)) else bool(self.keep_state))
+        r = act.req
+        try:
+            hist, counts, state = self.backend.collect(act.handle, keep)
+        except Exception as ex:  # this request's failure, not the server's
+            return [self._failed(r, act.admitted, ex)]
+        else:
+            res = Result(r.rid, hist, counts, state, r.arrival, act.admitted,
+                         self.clock(), int(counts.get("particle_steps", r.n * r.steps)))
+            self.results.append(res)
+            return [res]
+        finally:
+            self.backend.release(act.handle)
+            self.reserved -= self.backend.bytes_of(r)
+            self.active.remove(act)
 
     def _admit(self) -> list[Result]:
         failed = []
@@ -166,6 +170,9 @@ class Server:
             self.reserved += need
             self.peak_reserved = max(self.peak_reserved, self.reserved)
             self.active.append(_Active(req, handle, req.steps, self.clock()))
+        # a request of zero steps is done as admitted
+        for act in [a for a in self.active if a.remaining == 0 and not a.in_flight]:
+            failed.extend(self._finish(act))
         return failed
 
     def _launch(self):
@@ -235,7 +242,8 @@ class GpuBackend:
     """Requests on the CUDA library: one particle set per admitted request;
     one reusable mg_batch and stream per lane (a round whose members and step
     counts repeat the lane's previous round replays its captured CUDA graph);
-    a request's histogram is the snapshot of its final positions."""
+    a request's histogram is the snapshot of its final positions, fused into
+    its last round (device memory, read back through pinned host memory)."""
 
     def __init__(self, graphs: dict, precision: int, seed: int = 0, n_lanes: int = 2,
                  use_graph: bool = True, tuning=None):
@@ -265,19 +273,31 @@ class GpuBackend:
         g = self.graphs[req.graph]
         p = self.B.Particles(g, req.edge0, req.x0, seed=self.seed, instance=req.rid,
                              precision=self.precision)
-        return dict(req=req, p=p, graph=g)
+        return dict(req=req, p=p, graph=g, done=0, hist=None)
 
     def launch(self, lane: int, members):
         b = self.batches[lane]
-        sig = [(id(h["p"]), s) for h, s in members]
+        st = self.streams[lane]
+        torch = self.torch
+        plan = []
+        for h, s in members:
+            r = h["req"]
+            last = r.bins > 0 and h["done"] + s == r.steps
+            if last and h["hist"] is None:
+                with torch.cuda.stream(st):  # zeroed in order before the round
+                    h["hist"] = torch.zeros(h["graph"].n_edges * r.bins, dtype=torch.int32,
+                                            device="cuda")
+            plan.append((h, s, h["hist"] if last else None))
+        sig = [(id(h["p"]), s, 0 if hb is None else hb.data_ptr()) for h, s, hb in plan]
         if sig != self.last[lane]:  # else: replay the lane's captured graph
             b.clear()
-            for h, s in members:
+            for h, s, hb in plan:
                 r = h["req"]
-                b.add(h["p"], r.dt, s, r.M)
+                b.add(h["p"], r.dt, s, r.M, r.bins if hb is not None else 0, hb)
             self.last[lane] = sig
-        st = self.streams[lane]
         b.run(use_graph=self.use_graph, stream=st)
+        for h, s, _ in plan:
+            h["done"] += s
         ev = self.torch.cuda.Event()
         ev.record(st)
         return ev
@@ -286,18 +306,24 @@ class GpuBackend:
         return token.query()
 
     def collect(self, handle, keep_state: bool):
-        p = handle["p"]
+        p, r = handle["p"], handle["req"]
         p.synchronize()
         counts = p.counts()
-        hist = p.histogram(handle["req"].bins)  # snapshot of the final positions
+        if handle["hist"] is not None:  # fused into the last round
+            hp = self.torch.empty(handle["hist"].numel(), dtype=self.torch.int32, pin_memory=True)
+            hp.copy_(handle["hist"])
+            hist = hp.numpy().view(np.uint32)
+        else:  # no round ran (zero steps) or no bins
+            hist = p.histogram(r.bins) if r.bins > 0 else np.zeros(0, np.uint32)
         state = p.state() if keep_state else None
         return hist, counts, state
 
     def release(self, handle):
         for k, lane_sig in enumerate(self.last):
-            if lane_sig and any(pid == id(handle["p"]) for pid, _ in lane_sig):
+            if lane_sig and any(sg[0] == id(handle["p"]) for sg in lane_sig):
                 self.last[k] = None
                 self.batches[k].clear()
+        handle["hist"] = None
         handle["p"].close()
 
     def close(self):

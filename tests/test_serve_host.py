@@ -211,3 +211,22 @@ def test_rounds_sized_by_work():
     assert rounds[0] == [900]
     assert rounds[1] == [100] * 9
     assert be.steps_done == {0: 900, 1: 900}
+
+
+def test_zero_step_request_completes_at_admission():
+    """A request of zero steps needs no round: it is answered as soon as it
+    is admitted (before, it waited for a round that never came)."""
+    be = FakeBackend()
+    clk = FakeClock()
+    srv = serve.Server(be, mem_budget=10**9, n_lanes=1, chunk_steps=100, clock=clk)
+    srv.submit(serve.Request(0, "g", 50, 0, 1e-3))
+    srv.submit(serve.Request(1, "g", 50, 120, 1e-3))
+    done = srv.step()
+    assert [r.rid for r in done] == [0] and done[0].error is None
+    for _ in range(100):
+        if srv.idle():
+            break
+        clk.t += 1.0
+        srv.step()
+    assert srv.idle() and sorted(r.rid for r in srv.results) == [0, 1]
+    assert all(rid != 0 for tok in be.launches for rid, _ in tok["members"])
