@@ -579,6 +579,52 @@ def test_buffers_checked_before_any_launch(B):
     g.close()
 
 
+
+def test_large_host_inputs_checked_on_all_cores(B):
+    """Starting positions of a large set are checked on several host threads;
+    the error still names the first bad particle, and the set is unchanged by
+    a rejected reset.  Results read back to the host through the library's
+    pinned buffer are the same from several host threads at once."""
+    import threading
+    d = W.star_langevin(16)
+    n = 1 << 21
+    e, x = W.uniform_on_edges(d, n, 12)
+    g = B.Graph(d)
+    for bad in ([1_500_000, 1_900_000], [700_001], [n - 1]):
+        xb = x.copy()
+        xb[bad] = -1.0
+        with pytest.raises(B.MGError) as ei:
+            B.Particles(g, e, xb, seed=1, precision=B.MG_FP32_MIXED)
+        assert ei.value.status == B.MG_ERR_INVALID_ARG
+        assert f"particle {min(bad)}:" in str(ei.value), str(ei.value)
+    eb = e.copy()
+    eb[123_456] = 99
+    with pytest.raises(B.MGError) as ei:
+        B.Particles(g, eb, x, seed=1, precision=B.MG_FP32_MIXED)
+    assert "particle 123456: edge 99" in str(ei.value)
+    sets = [B.Particles(g, e, x, seed=s, precision=B.MG_FP32_MIXED) for s in range(4)]
+    for p in sets:
+        p.simulate(1e-3, 20, 16)
+        p.synchronize()
+    ref = [(p.counts(), p.histogram(8)) for p in sets]
+    got = [None] * len(sets)
+
+    def read(k):
+        for _ in range(5):
+            got[k] = (sets[k].counts(), sets[k].histogram(8))
+
+    threads = [threading.Thread(target=read, args=(k,)) for k in range(len(sets))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for (c0, h0), (c1, h1) in zip(ref, got):
+        assert np.array_equal(c0["exits"], c1["exits"]) and c0["particle_steps"] == c1["particle_steps"]
+        assert np.array_equal(h0, h1)
+    for p in sets:
+        p.close()
+    g.close()
+
 def test_overflow_to_infinity_is_reported(B):
     """A drift that pushes particles off to infinity on a semi-infinite edge
     (mu = +50 x: x grows by 5% a step) overflows binary32 within ~1800 steps:
