@@ -93,3 +93,26 @@ def test_star_langevin():
     assert np.all(d["src"] == 0) and np.array_equal(d["dst"], np.arange(1, 17))
     assert np.all(d["w_init"] == 1.0) and np.all(d["w_term"] == 1.0)
     assert "kind" not in d or not np.any(d["kind"])
+
+
+def test_batch_instances():
+    """512 uneven instances: half stars of 3..64 edges, half random trees of
+    100..10^4 edges (lognormal lengths, quadratic potentials), N from 2^12 to
+    2^22, steps from 100 to 5000, dt = 1e-3, M = 16; the totals the batched
+    benchmark reports."""
+    insts = W.batch_instances(512)
+    assert len(insts) == 512 and [it["instance"] for it in insts] == list(range(512))
+    stars, trees = insts[0::2], insts[1::2]
+    ks = [len(it["graph"]["src"]) for it in stars]
+    es = [len(it["graph"]["src"]) for it in trees]
+    assert min(ks) >= 3 and max(ks) <= 64 and len(set(ks)) > 30
+    assert min(es) >= 100 and max(es) <= 10_000 and max(es) > 5_000
+    for it in trees[:8]:
+        g = it["graph"]
+        assert len(g["src"]) == g["n_vertices"] - 1  # a tree
+    n = np.array([it["n"] for it in insts])
+    steps = np.array([it["steps"] for it in insts])
+    assert n.min() >= 2**12 and n.max() <= 2**22
+    assert steps.min() >= 100 and steps.max() <= 5000
+    assert all(it["dt"] == 1e-3 and it["M"] == 16 for it in insts)
+    assert int(n.sum()) == 326_674_086 and int((n * steps).sum()) == 889_336_178_611
