@@ -110,12 +110,12 @@ double or_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t n) {
 uint32_t or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j) {
   uint32_t key[2], ctr[4], w[4];
   key_of_seed(seed, key);
-  ctr[0] = j;
+  ctr[0] = j >> 2; /* four draws per block */
   ctr[1] = pid;
   ctr[2] = 1u; /* tag 1: draws of vertex hits */
   ctr[3] = instance;
   or_philox4x32_10(ctr, key, w);
-  return w[0];
+  return w[j & 3u];
 }
 
 /* ------------------------------------------------------------------- graph */

@@ -41,7 +41,8 @@ void or_box_muller(uint32_t wa, uint32_t wb, double* z_cos, double* z_sin);
 double or_normal(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t n);
 
 /* The uniform 32-bit draw of the j-th vertex hit of particle pid (it picks
- * the next edge): word w0 of block (j, pid, 1, instance). */
+ * the next edge): word w[j&3] of block (j>>2, pid, 1, instance), four draws
+ * per block. */
 uint32_t or_split_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t j);
 
 /* ----------------------------------------------------------------- graph */

@@ -111,6 +111,22 @@ def test_split_draws(oracle):
         assert stats.chisquare(counts).pvalue > 1e-4
 
 
+def test_split_draws_of_one_block_are_independent(oracle):
+    """Four consecutive hits share a Philox block (one word each): the pairs
+    (u_j, u_j+1) -- within a block (j mod 4 = 0, 1, 2) and across a block
+    boundary (j mod 4 = 3) -- are uniform on the 16 x 16 grid of their top 4
+    bits, and the four words of a block differ."""
+    us = np.array([[oracle.split_draw(3, 0, pid, j) for j in range(64)] for pid in range(256)],
+                  dtype=np.uint64)
+    hi = (us >> 28).astype(np.int64)
+    for r in range(4):
+        a, b = hi[:, r:63:4].reshape(-1), hi[:, r + 1:64:4].reshape(-1)
+        counts = np.bincount(a * 16 + b, minlength=256)
+        assert stats.chisquare(counts).pvalue > 1e-4, r
+    for r in range(3):
+        assert np.all(us[:, r::4] != us[:, r + 1::4])
+
+
 def test_streams_are_distinct(oracle):
     # tag, pid, instance and seed each change the stream
     a = oracle.normal(1, 0, 0, 0)
