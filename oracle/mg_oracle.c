@@ -34,6 +34,12 @@
  *  R8  Exit counts: a sub-step that starts at a vertex and ends inside the
  *      edge counts one exit through that (vertex, edge, end) slot; this is
  *      the event whose law Corollary 1 states.
+ *  R15 Position-dependent diffusion (the edge generator allows any C^1
+ *      sigma_e; here the affine sigma_e(x) = sigma_e + sigma1_e x): like the
+ *      drift, it is evaluated at the sub-step's starting point x_s (Algorithm
+ *      1 evaluates mu_e and sigma_e there), so the increment is
+ *      sigma_e(x_s) sqrt(h) W and the split's quadratic keeps B =
+ *      sigma_e(x_s) sqrt(h) W.
  */
 #include "mg_oracle.h"
 
@@ -125,7 +131,7 @@ static void* xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
 void or_graph_free(or_graph* g) {
   if (!g) return;
   free(g->src); free(g->dst); free(g->length); free(g->c0); free(g->c1);
-  free(g->sigma); free(g->w_init); free(g->w_term); free(g->hist_range);
+  free(g->sigma); free(g->sigma1); free(g->w_init); free(g->w_term); free(g->hist_range);
   free(g->kind); free(g->vtx_off); free(g->slot_edge); free(g->slot_end);
   free(g->slot_T); free(g->slot_of_end);
   free(g);
@@ -161,6 +167,7 @@ int or_graph_build(int32_t V, int32_t E, const int32_t* src, const int32_t* dst,
   g->src = (int32_t*)xcalloc(E, 4); g->dst = (int32_t*)xcalloc(E, 4);
   g->length = (double*)xcalloc(E, 8); g->c0 = (double*)xcalloc(E, 8);
   g->c1 = (double*)xcalloc(E, 8); g->sigma = (double*)xcalloc(E, 8);
+  g->sigma1 = (double*)xcalloc(E, 8); /* constant diffusion unless set */
   g->w_init = (double*)xcalloc(E, 8); g->w_term = (double*)xcalloc(E, 8);
   g->hist_range = (double*)xcalloc(E, 8);
   g->kind = (uint8_t*)xcalloc(V, 1);
@@ -227,6 +234,19 @@ int or_graph_build(int32_t V, int32_t E, const int32_t* src, const int32_t* dst,
   }
   free(wslot);
   *out = g;
+  return 0;
+}
+
+int or_graph_set_sigma1(or_graph* g, const double* sigma1) {
+  for (int32_t e = 0; e < g->n_edges; ++e) {
+    if (!isfinite(sigma1[e])) return -1;
+    if (g->dst[e] < 0) {
+      if (sigma1[e] < 0.0) return -1;
+    } else if (!(g->sigma[e] + sigma1[e] * g->length[e] > 0.0)) {
+      return -1;
+    }
+  }
+  memcpy(g->sigma1, sigma1, 8 * (size_t)g->n_edges);
   return 0;
 }
 
@@ -322,8 +342,9 @@ int or_em_step(const or_graph* g, or_particle* p, double dt, int32_t M, or_draws
     /* Euler-Maruyama sub-step (Eq. of the scheme on the real line) */
     double xs = p->x;
     double mu = g->c0[e] + g->c1[e] * xs;
+    double sig = g->sigma[e] + g->sigma1[e] * xs; /* R15 */
     double a = mu * h;
-    double b = g->sigma[e] * sqrt(h) * W;
+    double b = sig * sqrt(h) * W;
     double xt = xs + a + b;
 
     double tol = 1e-9 * ((isfinite(l) && l > 1.0) ? l : 1.0);

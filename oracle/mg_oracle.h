@@ -61,6 +61,9 @@ typedef struct {
    * range (l_e unless the edge is semi-infinite). */
   int32_t *src, *dst;
   double *length, *c0, *c1, *sigma, *w_init, *w_term, *hist_range;
+  /* diffusion slope: sigma_e(x) = sigma + sigma1 x (zero unless set by
+   * or_graph_set_sigma1) */
+  double* sigma1;
   uint8_t* kind; /* per vertex */
   /* CSR of vertex-edge incidences ("slots"), ordered by (vertex, edge id,
    * init end before term end). */
@@ -80,6 +83,11 @@ int or_graph_build(int32_t n_vertices, int32_t n_edges, const int32_t* src,
                    const double* w_term, const double* hist_range,
                    const uint8_t* kind, or_graph** out);
 void or_graph_free(or_graph* g);
+/* Position-dependent diffusion sigma_e(x) = sigma_e + sigma1_e x (x from
+ * e_init), positive on the whole edge: sigma_e + sigma1_e l_e > 0 on a
+ * finite edge, sigma1_e >= 0 on a semi-infinite one.  Returns 0, or a
+ * negative code (nothing changed) for an invalid slope. */
+int or_graph_set_sigma1(or_graph* g, const double* sigma1);
 int32_t or_graph_n_slots(const or_graph* g);
 void or_graph_slots(const or_graph* g, int32_t* vtx_off, int32_t* slot_edge,
                     uint8_t* slot_end, uint64_t* slot_T);

@@ -70,6 +70,8 @@ def _declare(L):
     L.or_graph_build.argtypes = [i32, i32, _p(i32), _p(i32), _p(dbl), _p(dbl), _p(dbl), _p(dbl),
                                  _p(dbl), _p(dbl), _p(dbl), _p(u8), C.POINTER(C.c_void_p)]
     L.or_graph_build.restype = C.c_int
+    L.or_graph_set_sigma1.argtypes = [C.c_void_p, _p(dbl)]
+    L.or_graph_set_sigma1.restype = C.c_int
     L.or_graph_free.argtypes = [C.c_void_p]
     L.or_graph_free.restype = None
     L.or_graph_n_slots.argtypes = [C.c_void_p]
@@ -140,7 +142,7 @@ class Graph:
     """Oracle copy of a metric graph (arrays as in the library's description)."""
 
     def __init__(self, n_vertices, src, dst, length, c0, c1, sigma, w_init, w_term,
-                 hist_range=None, kind=None):
+                 hist_range=None, kind=None, sigma1=None):
         E = len(src)
         self.n_vertices = int(n_vertices)
         self.n_edges = E
@@ -169,13 +171,18 @@ class Graph:
         if rc != 0:
             raise ValueError("oracle: invalid graph description")
         self._h = h
+        if sigma1 is not None:
+            self._s1 = np.ascontiguousarray(np.broadcast_to(sigma1, (E,)), dtype=np.float64)
+            if lib().or_graph_set_sigma1(h, _ptr(self._s1, C.c_double)) != 0:
+                raise ValueError("oracle: invalid diffusion slope")
         self.n_slots = lib().or_graph_n_slots(h)
 
     @classmethod
     def from_desc(cls, d):
         """Build from a dict with the keys of a workload graph description."""
         return cls(d["n_vertices"], d["src"], d["dst"], d["length"], d["c0"], d["c1"],
-                   d["sigma"], d["w_init"], d["w_term"], d.get("hist_range"), d.get("kind"))
+                   d["sigma"], d["w_init"], d["w_term"], d.get("hist_range"), d.get("kind"),
+                   d.get("sigma1"))
 
     def __del__(self):
         h = getattr(self, "_h", None)

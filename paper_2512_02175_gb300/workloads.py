@@ -107,6 +107,17 @@ def line_as_star(half_length: float = 10.0, sigma: float = 1.0):
     return _desc(3, [0, 0], [1, 2], [half_length, half_length], 0.0, 0.0, sigma, 1.0, 1.0)
 
 
+def line_affine_sigma(slopes=(1.0, 0.5), length: float = 1.0, sigma0: float = 1.0):
+    """Two edges of length ``length`` glued at vertex 0 with b = 1/2, no
+    drift, position-dependent diffusion sigma_e(x) = sigma0 + slopes[e] x
+    (the same sigma0 at the shared vertex), reflecting far ends."""
+    k = len(slopes)
+    d = _desc(k + 1, np.zeros(k, np.int32), np.arange(1, k + 1, dtype=np.int32),
+              np.full(k, length), 0.0, 0.0, sigma0, 1.0, 1.0)
+    d["sigma1"] = np.asarray(slopes, np.float64)
+    return d
+
+
 def random_tree(n_edges: int, seed: int, sigma_range=(0.5, 1.5)):
     """Uniform random labelled tree (Pruefer sequence), lognormal lengths
     (median 1, sigma_log 0.5), quadratic potentials as in ``star_langevin``,
