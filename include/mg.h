@@ -93,6 +93,13 @@ typedef struct {
                                   semi-infinite edge) */
   const uint8_t* vertex_kind;  /* [n_vertices] mg_vertex_kind, or NULL (all
                                   standard) */
+  const double* sigma_slope;   /* NULL (constant diffusion), or the slope k_e of a
+                                  position-dependent diffusion sigma_e(x) = sigma_e
+                                  + k_e x (x from e_init; the edge generator allows
+                                  any C^1 sigma_e, Section 2.2), evaluated at each
+                                  sub-step's starting point as Algorithm 1 evaluates
+                                  the coefficients; finite, with sigma_e(x) > 0 on
+                                  the whole edge (k_e >= 0 on a semi-infinite one) */
 } mg_graph_desc;
 
 /* ---------------------------------------------------------------- memory */
@@ -117,7 +124,8 @@ mg_status mg_set_allocator(mg_alloc_fn alloc, mg_free_fn free_fn, void* ctx);
  * device.  MG_ERR_INVALID_ARG for: a vertex id out of range; a length <= 0 or
  * NaN, infinite on a finite edge or finite on a semi-infinite one; sigma <= 0;
  * a non-finite drift; a negative weight; a standard vertex with incident
- * slots whose weights sum to 0; a bad hist_range or vertex kind. */
+ * slots whose weights sum to 0; a bad hist_range or vertex kind; a slope that
+ * is not finite or lets sigma_e(x) reach 0 on the edge. */
 mg_status mg_graph_create(const mg_graph_desc* desc, mg_graph* out);
 
 /* MG_ERR_BUSY while particle sets created on the graph are alive. */
@@ -202,7 +210,7 @@ mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t s
 mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32_t max_splits_M,
                       int32_t hist_bins, uint32_t* hist_out, void* stream);
 
-/* Time-averaged occupancy.  Section 5.1 estimates a steady-state density by a
+/* Time-averaged occupancy.  Section 4.1 estimates a steady-state density by a
  * histogram of the particles after a long run; averaging snapshots over time
  * lowers its noise.  Advances every particle by `steps` EM-Steps exactly as
  * mg_simulate does (bit-identical results) and ADDS the snapshot histogram of
@@ -282,14 +290,18 @@ mg_status mg_histogram(mg_particles p, int32_t bins, uint32_t* out, int out_on_d
  * MG_ERR_INVALID_ARG.  Nothing is allocated: no cudaMalloc, cudaFree or
  * allocator hook is called.  out[n_edges * bins] is host memory, overwritten;
  * the call synchronises `stream`.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make it before any stream
- * capture.  All calls share the one array, which keeps the previous call's
- * counts (each call clears what it uses): calls that overlap on the GPU, from
- * different streams or threads, race. */
+ * array's device address (cudaGetSymbolAddress) and keeps it; if the
+ * library's device code is not loaded on that device yet (CUDA's lazy module
+ * loading), that lookup loads it, reserving the array, and may synchronise
+ * the device -- so make the first call during set-up, before any stream
+ * capture.  cudaDeviceReset frees the array: do not call this entry point on
+ * a device after resetting it.  All calls share the one array, which keeps
+ * the previous call's counts (each call clears what it uses): calls that
+ * overlap on the GPU, from different streams or threads, race. */
 mg_status mg_histogram_static(mg_particles p, int32_t bins, uint32_t* out, void* stream);
 
 /* Snapshot histogram with bins of any width per edge (the paper's densities
- * are histograms of the particles' positions, Section 5.1; here each edge
+ * are histograms of the particles' positions, Section 4.1; here each edge
  * takes its own bin boundaries).  bin_offsets[n_edges + 1] (host, int32):
  * the bins of edge e are bin_offsets[e] .. bin_offsets[e+1]-1, bin_offsets[0]
  * = 0, non-decreasing (an edge may have none); bin_upper[bin_offsets[n_edges]]
@@ -327,6 +339,26 @@ mg_status mg_state_get(mg_particles p, int32_t* edge, double* x, uint32_t* n_dra
 mg_status mg_state_set(mg_particles p, const int32_t* edge, const double* x,
                        const uint32_t* n_draw, const uint32_t* hits, const uint32_t* first_hits,
                        const uint32_t* flags, uint64_t step, void* stream);
+
+/* The hitting fraction of a split (Section 3, the partial sub-step of
+ * Algorithms 1 and 2): a sub-step x + a + b (a = mu_e h, b = sigma_e sqrt(h) W)
+ * that ends beyond a vertex at distance C >= 0 reaches it after the fraction
+ * alpha = s^2 of its time h, s the first root in [0, 1] of A s^2 + B s + C = 0
+ * (A = a, B = b at e_init; A = -a, B = -b at e_term).  Computes s for n
+ * coefficient triples with the device function that precision mode `mode`
+ * uses in its kernels:
+ *   MG_FP64        the closed form in binary64: d = sqrt(max(B^2 - 4AC, 0)),
+ *                  s = (-B - d) / (2A) for B > 0, 2C / (-B + d) otherwise,
+ *                  -C / B for A = 0, clamped to [0, 1] (correctly rounded
+ *                  binary64 square root and quotient);
+ *   MG_FP32_MIXED  the binary64 root of the FP32-mixed mode (the binary32
+ *                  coefficients widened exactly; see mg_precision);
+ *   MG_FP32        the binary32 root with the hardware's approximate square
+ *                  root and reciprocal.
+ * A, B, C: device, binary32 [n] (coefficients as the binary32 modes form
+ * them); s: device, binary64 [n], overwritten.  n >= 0.  Stream-ordered. */
+mg_status mg_hit_root(int32_t mode, int64_t n, const float* A, const float* B, const float* C,
+                      double* s, void* stream);
 
 /* n, precision and step counter of a set; any pointer may be NULL. */
 mg_status mg_particles_info(mg_particles p, int64_t* n, int32_t* precision, uint64_t* step);

@@ -151,7 +151,7 @@ void or_simulate(const or_graph* g, int64_t n, const uint32_t* pid, int32_t* edg
 void or_histogram(const or_graph* g, int64_t n, const int32_t* edge, const double* x,
                   int32_t B, uint64_t* hist);
 
-/* Snapshot histogram with bins of any width per edge (Section 5.1 estimates
+/* Snapshot histogram with bins of any width per edge (Section 4.1 estimates
  * densities by histograms; the bins of edge e are off[e] .. off[e+1]-1 with
  * upper boundaries up[j], increasing within the edge).  A living particle at
  * x on e counts in the first bin j of e with x < up[j], else in e's last bin;

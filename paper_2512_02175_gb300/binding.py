@@ -45,6 +45,7 @@ class mg_graph_desc(C.Structure):
         ("drift_c1", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
         ("weight_init", C.POINTER(C.c_double)), ("weight_term", C.POINTER(C.c_double)),
         ("hist_range", C.POINTER(C.c_double)), ("vertex_kind", C.POINTER(C.c_uint8)),
+        ("sigma_slope", C.POINTER(C.c_double)),
     ]
 
 
@@ -58,7 +59,7 @@ SYMBOLS = [
     "mg_simulate_sampled", "mg_histogram_binned",
     "mg_simulate",
     "mg_synchronize", "mg_histogram", "mg_histogram_static", "mg_exit_counts", "mg_counters_reset", "mg_state_get",
-    "mg_state_set", "mg_particles_info", "mg_last_error", "mg_version",
+    "mg_state_set", "mg_particles_info", "mg_hit_root", "mg_last_error", "mg_version",
     "mg_batch_create", "mg_batch_add", "mg_batch_clear", "mg_batch_set_tuning", "mg_batch_run",
     "mg_batch_info", "mg_batch_destroy",
 ]
@@ -120,6 +121,7 @@ def _declare(L):
         "mg_batch_info": ([vp, vp, vp, vp], st),
         "mg_batch_destroy": ([vp], st),
         "mg_last_error": ([], C.c_char_p),
+        "mg_hit_root": ([i32, i64, vp, vp, vp, vp, vp], st),
         "mg_version": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -282,6 +284,9 @@ def _desc_struct(d):
     s.weight_term = arr("w_term", np.float64, C.c_double)
     s.hist_range = arr("hist_range", np.float64, C.c_double, optional=True)
     s.vertex_kind = arr("kind", np.uint8, C.c_uint8, optional=True)
+    if d.get("sigma1") is not None:  # position-dependent diffusion sigma + sigma1 x
+        d = dict(d, sigma1=np.broadcast_to(np.asarray(d["sigma1"], np.float64), (s.n_edges,)))
+    s.sigma_slope = arr("sigma1", np.float64, C.c_double, optional=True)
     return s, keep
 
 
@@ -408,6 +413,19 @@ def mg_histogram_static(p, bins, out, stream=None):
     _host_out(out, np.uint32, None if sz is None else sz[1] * int(bins), "out")
     _check(load().mg_histogram_static(p, int(bins), _ptr(out), _stream_ptr(stream)))
     return out
+
+
+def mg_hit_root(mode, A, B, C, s, stream=None):
+    """Hitting-fraction roots of the coefficient triples (A, B, C) (CUDA
+    float32 tensors of one length) into ``s`` (CUDA float64 tensor) by the
+    device function of precision mode ``mode`` (see include/mg.h)."""
+    n = int(A.numel())
+    for t, what in ((A, "A"), (B, "B"), (C, "C")):
+        _device_arr(t, ("float32",), n, what, exact=True)
+    _device_arr(s, ("float64",), n, "s", exact=True)
+    _check(load().mg_hit_root(int(mode), n, _ptr(A), _ptr(B), _ptr(C), _ptr(s),
+                              _stream_ptr(stream)))
+    return s
 
 
 def mg_exit_counts(p, n_slots, n_vertices, stream=None):

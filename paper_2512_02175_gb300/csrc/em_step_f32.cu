@@ -4,114 +4,98 @@
 #include "mg_em_step.cuh"
 #include "mg_histogram.cuh"
 #include "mg_launch.h"
+#include "mg_launch_impl.cuh"
 
 namespace mg {
 
-template <int kMode>
-static void set_smem_attributes() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(em_step_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(em_range_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(em_batch_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    done = true;
-  }
-}
-
+// Modes of this unit: FP32-mixed and FP32, each with constant or
+// position-dependent (kVarSigma) diffusion.
 cudaError_t launch_em_step_f32x(int mode, const SimArgs& a, const Keys& k, size_t smem,
                                 cudaStream_t st) {
-  const int64_t grid = (a.n + a.range - 1) / a.range;
-  const bool ranged = a.range > kBlock;
-  if (mode == kModeMixed) {
-    set_smem_attributes<kModeMixed>();
-    if (ranged) em_range_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
-    else em_step_kernel<kModeMixed><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
-  } else {
-    set_smem_attributes<kModeF32>();
-    if (ranged) em_range_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
-    else em_step_kernel<kModeF32><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
+  switch (mode) {
+    case kModeMixed: return launch_step_t<kModeMixed>(a, k, smem, st);
+    case kModeF32: return launch_step_t<kModeF32>(a, k, smem, st);
+    case kModeMixed | kVarSigma: return launch_step_t<kModeMixed | kVarSigma>(a, k, smem, st);
+    case kModeF32 | kVarSigma: return launch_step_t<kModeF32 | kVarSigma>(a, k, smem, st);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 int em_step_blocks_per_sm_f32x(int mode, size_t smem) {
-  int nb = 0;
-  if (mode == kModeMixed) {
-    set_smem_attributes<kModeMixed>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeMixed>, kBlock, smem);
-  } else {
-    set_smem_attributes<kModeF32>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeF32>, kBlock, smem);
+  switch (mode) {
+    case kModeMixed: return step_blocks_per_sm_t<kModeMixed>(smem);
+    case kModeF32: return step_blocks_per_sm_t<kModeF32>(smem);
+    case kModeMixed | kVarSigma: return step_blocks_per_sm_t<kModeMixed | kVarSigma>(smem);
+    case kModeF32 | kVarSigma: return step_blocks_per_sm_t<kModeF32 | kVarSigma>(smem);
+    default: return 0;
   }
-  return nb;
 }
 
 int em_step_blocks_per_sm(int mode, size_t smem) {
-  return mode == kModeF64 ? em_step_blocks_per_sm_f64(smem)
-                          : em_step_blocks_per_sm_f32x(mode, smem);
+  return prec_of(mode) == kModeF64 ? em_step_blocks_per_sm_f64(mode, smem)
+                                   : em_step_blocks_per_sm_f32x(mode, smem);
 }
 
 int em_range_blocks_per_sm_f32x(int mode, size_t smem) {
-  int nb = 0;
-  if (mode == kModeMixed) {
-    set_smem_attributes<kModeMixed>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeMixed>, kBlock, smem);
-  } else {
-    set_smem_attributes<kModeF32>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeF32>, kBlock, smem);
+  switch (mode) {
+    case kModeMixed: return range_blocks_per_sm_t<kModeMixed>(smem);
+    case kModeF32: return range_blocks_per_sm_t<kModeF32>(smem);
+    case kModeMixed | kVarSigma: return range_blocks_per_sm_t<kModeMixed | kVarSigma>(smem);
+    case kModeF32 | kVarSigma: return range_blocks_per_sm_t<kModeF32 | kVarSigma>(smem);
+    default: return 0;
   }
-  return nb;
 }
 
 int em_range_blocks_per_sm(int mode, size_t smem) {
-  return mode == kModeF64 ? em_range_blocks_per_sm_f64(smem)
-                          : em_range_blocks_per_sm_f32x(mode, smem);
+  return prec_of(mode) == kModeF64 ? em_range_blocks_per_sm_f64(mode, smem)
+                                   : em_range_blocks_per_sm_f32x(mode, smem);
 }
 
 cudaError_t launch_em_batch_f32x(int mode, const SimArgs* insts, const BatchItem* items,
                                  int32_t n_items, uint32_t* head, const Keys& k, size_t smem,
                                  int blocks, cudaStream_t st) {
-  if (mode == kModeMixed) {
-    set_smem_attributes<kModeMixed>();
-    em_batch_kernel<kModeMixed><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
-  } else {
-    set_smem_attributes<kModeF32>();
-    em_batch_kernel<kModeF32><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
+  switch (mode) {
+    case kModeMixed:
+      return launch_batch_t<kModeMixed>(insts, items, n_items, head, k, smem, blocks, st);
+    case kModeF32:
+      return launch_batch_t<kModeF32>(insts, items, n_items, head, k, smem, blocks, st);
+    case kModeMixed | kVarSigma:
+      return launch_batch_t<kModeMixed | kVarSigma>(insts, items, n_items, head, k, smem, blocks,
+                                                    st);
+    case kModeF32 | kVarSigma:
+      return launch_batch_t<kModeF32 | kVarSigma>(insts, items, n_items, head, k, smem, blocks,
+                                                  st);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 int em_batch_blocks_per_sm_f32x(int mode, size_t smem) {
-  int nb = 0;
-  if (mode == kModeMixed) {
-    set_smem_attributes<kModeMixed>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeMixed>, kBlock, smem);
-  } else {
-    set_smem_attributes<kModeF32>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeF32>, kBlock, smem);
+  switch (mode) {
+    case kModeMixed: return batch_blocks_per_sm_t<kModeMixed>(smem);
+    case kModeF32: return batch_blocks_per_sm_t<kModeF32>(smem);
+    case kModeMixed | kVarSigma: return batch_blocks_per_sm_t<kModeMixed | kVarSigma>(smem);
+    case kModeF32 | kVarSigma: return batch_blocks_per_sm_t<kModeF32 | kVarSigma>(smem);
+    default: return 0;
   }
-  return nb;
 }
 
 cudaError_t launch_em_step(int mode, const SimArgs& a, const Keys& k, size_t smem,
                            cudaStream_t st) {
-  return mode == kModeF64 ? launch_em_step_f64(a, k, smem, st)
-                          : launch_em_step_f32x(mode, a, k, smem, st);
+  return prec_of(mode) == kModeF64 ? launch_em_step_f64(mode, a, k, smem, st)
+                                   : launch_em_step_f32x(mode, a, k, smem, st);
 }
 
 cudaError_t launch_em_batch(int mode, const SimArgs* insts, const BatchItem* items, int32_t n_items,
                             uint32_t* head, const Keys& k, size_t smem, int blocks,
                             cudaStream_t st) {
-  return mode == kModeF64 ? launch_em_batch_f64(insts, items, n_items, head, k, smem, blocks, st)
-                          : launch_em_batch_f32x(mode, insts, items, n_items, head, k, smem,
-                                                 blocks, st);
+  return prec_of(mode) == kModeF64
+             ? launch_em_batch_f64(mode, insts, items, n_items, head, k, smem, blocks, st)
+             : launch_em_batch_f32x(mode, insts, items, n_items, head, k, smem, blocks, st);
 }
 
 int em_batch_blocks_per_sm(int mode, size_t smem) {
-  return mode == kModeF64 ? em_batch_blocks_per_sm_f64(smem) : em_batch_blocks_per_sm_f32x(mode, smem);
+  return prec_of(mode) == kModeF64 ? em_batch_blocks_per_sm_f64(mode, smem)
+                                   : em_batch_blocks_per_sm_f32x(mode, smem);
 }
 
 cudaError_t launch_histogram_f32(const GraphView& g, const int32_t* edge, const void* x, int64_t n,
@@ -206,6 +190,38 @@ cudaError_t launch_init_state(const GraphView& g, const int32_t* edge0, const do
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   zero_counters_kernel<<<(unsigned)grid, kBlock, 0, st>>>(s, n);
+  return cudaGetLastError();
+}
+
+// The hitting-fraction root of n coefficient triples by the device function
+// of precision mode `mode` (mg_hit_root).
+__global__ void hit_root_kernel(int32_t mode, int64_t n, const float* __restrict__ A,
+                                const float* __restrict__ B, const float* __restrict__ C,
+                                double* __restrict__ s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = A[i], b = B[i], c = C[i];
+    double r;
+    if (mode == kModeF32) {
+      r = widen_f32(hit_root_fast(a, b, c));
+    } else if (mode == kModeMixed) {
+      r = hit_root_f64_newton(a, b, c);
+    } else {
+      r = hit_root_f64_closed(a, b, c);
+    }
+    s[i] = r;
+  }
+}
+
+cudaError_t launch_hit_root(int32_t mode, int64_t n, const float* A, const float* B,
+                            const float* C, double* s, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  hit_root_kernel<<<(unsigned)grid, kBlock, 0, st>>>(mode, n, A, B, C, s);
   return cudaGetLastError();
 }
 

@@ -1,61 +1,45 @@
-// em_step_f64.cu -- binary64 instantiation of the fused EM-Step kernel and of
-// the histogram kernel.  Built without floating-point contraction
+// em_step_f64.cu -- binary64 instantiations of the fused EM-Step kernels
+// (constant and position-dependent diffusion) and of the histogram kernels.  Built without floating-point contraction
 // (--fmad=false) so that every binary64 operation rounds exactly as written,
 // in the same order as the plain CPU reference of the scheme.
 #include "mg_em_step.cuh"
 #include "mg_histogram.cuh"
 #include "mg_launch.h"
+#include "mg_launch_impl.cuh"
 
 namespace mg {
 
-static void set_smem_attributes() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(em_step_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(em_range_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(em_batch_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    done = true;
-  }
+// Modes of this unit: binary64 with constant or position-dependent
+// (kVarSigma) diffusion.
+constexpr int kF64Var = kModeF64 | kVarSigma;
+
+cudaError_t launch_em_step_f64(int mode, const SimArgs& a, const Keys& k, size_t smem,
+                               cudaStream_t st) {
+  return var_sigma(mode) ? launch_step_t<kF64Var>(a, k, smem, st)
+                         : launch_step_t<kModeF64>(a, k, smem, st);
 }
 
-cudaError_t launch_em_step_f64(const SimArgs& a, const Keys& k, size_t smem, cudaStream_t st) {
-  set_smem_attributes();
-  const int64_t grid = (a.n + a.range - 1) / a.range;
-  if (a.range > kBlock) em_range_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
-  else em_step_kernel<kModeF64><<<(unsigned)grid, kBlock, smem, st>>>(a, k);
-  return cudaGetLastError();
+int em_step_blocks_per_sm_f64(int mode, size_t smem) {
+  return var_sigma(mode) ? step_blocks_per_sm_t<kF64Var>(smem)
+                         : step_blocks_per_sm_t<kModeF64>(smem);
 }
 
-int em_step_blocks_per_sm_f64(size_t smem) {
-  set_smem_attributes();
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_step_kernel<kModeF64>, kBlock, smem);
-  return nb;
+int em_range_blocks_per_sm_f64(int mode, size_t smem) {
+  return var_sigma(mode) ? range_blocks_per_sm_t<kF64Var>(smem)
+                         : range_blocks_per_sm_t<kModeF64>(smem);
 }
 
-int em_range_blocks_per_sm_f64(size_t smem) {
-  set_smem_attributes();
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_range_kernel<kModeF64>, kBlock, smem);
-  return nb;
+cudaError_t launch_em_batch_f64(int mode, const SimArgs* insts, const BatchItem* items,
+                                int32_t n_items, uint32_t* head, const Keys& k, size_t smem,
+                                int blocks, cudaStream_t st) {
+  return var_sigma(mode)
+             ? launch_batch_t<kF64Var>(insts, items, n_items, head, k, smem, blocks, st)
+             : launch_batch_t<kModeF64>(insts, items, n_items, head, k, smem, blocks, st);
 }
 
-cudaError_t launch_em_batch_f64(const SimArgs* insts, const BatchItem* items, int32_t n_items,
-                                uint32_t* head, const Keys& k, size_t smem, int blocks,
-                                cudaStream_t st) {
-  set_smem_attributes();
-  em_batch_kernel<kModeF64><<<blocks, kBlock, smem, st>>>(insts, items, n_items, head, k);
-  return cudaGetLastError();
-}
-
-int em_batch_blocks_per_sm_f64(size_t smem) {
-  set_smem_attributes();
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, em_batch_kernel<kModeF64>, kBlock, smem);
-  return nb;
+int em_batch_blocks_per_sm_f64(int mode, size_t smem) {
+  return var_sigma(mode) ? batch_blocks_per_sm_t<kF64Var>(smem)
+                         : batch_blocks_per_sm_t<kModeF64>(smem);
 }
 
 cudaError_t launch_histogram_f64(const GraphView& g, const int32_t* edge, const void* x, int64_t n,

@@ -186,6 +186,7 @@ struct mg_graph_s {
   std::vector<int32_t> src, dst, vtx_off, slot_edge, slot_of_end;
   std::vector<uint8_t> slot_end, kind;
   bool has_absorbing = false;  // particles can die
+  bool var_sigma = false;      // some edge has a nonzero diffusion slope
   std::vector<uint64_t> slot_T;
   std::vector<double> length, range;
   // device tables (one allocation)
@@ -224,7 +225,8 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
                               {d->length, "length"}, {d->drift_c0, "drift_c0"},
                               {d->drift_c1, "drift_c1"}, {d->sigma, "sigma"},
                               {d->weight_init, "weight_init"}, {d->weight_term, "weight_term"},
-                              {d->hist_range, "hist_range"}, {d->vertex_kind, "vertex_kind"}});
+                              {d->hist_range, "hist_range"}, {d->vertex_kind, "vertex_kind"},
+                              {d->sigma_slope, "sigma_slope"}});
     if (s != MG_OK) return s;
   }
   for (int32_t e = 0; e < E; ++e) {
@@ -247,6 +249,14 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
       return fail(MG_ERR_INVALID_ARG, "edge %d: weight_term must be >= 0", e);
     if (d->hist_range && !finite_pos(d->hist_range[e]))
       return fail(MG_ERR_INVALID_ARG, "edge %d: hist_range must be finite and > 0", e);
+    if (d->sigma_slope) {
+      const double k = d->sigma_slope[e];
+      if (!std::isfinite(k))
+        return fail(MG_ERR_INVALID_ARG, "edge %d: sigma_slope must be finite", e);
+      if (t == -1 ? !(k >= 0.0) : !(d->sigma[e] + k * L > 0.0))
+        return fail(MG_ERR_INVALID_ARG, "edge %d: sigma_e(x) = sigma + sigma_slope x must stay "
+                    "> 0 on the edge", e);
+    }
   }
   if (d->vertex_kind)
     for (int32_t v = 0; v < V; ++v)
@@ -266,6 +276,14 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   if (d->vertex_kind) g->kind.assign(d->vertex_kind, d->vertex_kind + V);
   for (int32_t v = 0; v < V; ++v)
     if (g->kind[v] == MG_VERTEX_ABSORBING) g->has_absorbing = true;
+  std::vector<double> s1_64(E, 0.0);
+  std::vector<float> s1_32(E, 0.0f);
+  if (d->sigma_slope)
+    for (int32_t e = 0; e < E; ++e) {
+      s1_64[e] = d->sigma_slope[e];
+      s1_32[e] = (float)d->sigma_slope[e];
+      if (s1_64[e] != 0.0) g->var_sigma = true;
+    }
 
   // Slots by counting sort on the vertex: each edge contributes its init end
   // then its term end, edges in id order, so within a vertex the slots are
@@ -360,7 +378,9 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   const size_t ov = a256(os + S * sizeof(mg::SlotRec));
   const size_t og = a256(ov + V * sizeof(mg::VtxRec));
   const size_t orr = a256(og + (size_t)G * sizeof(int32_t));
-  const size_t total = a256(orr + E * sizeof(double));
+  const size_t os32 = a256(orr + E * sizeof(double));
+  const size_t os64 = a256(os32 + E * sizeof(float));
+  const size_t total = a256(os64 + E * sizeof(double));
   mg_status st = dev_alloc(g->buf, total, nullptr);
   if (st != MG_OK) {
     delete g;
@@ -373,6 +393,8 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   memcpy(host.data() + ov, vtx.data(), V * sizeof(mg::VtxRec));
   memcpy(host.data() + og, guide.data(), (size_t)G * sizeof(int32_t));
   memcpy(host.data() + orr, g->range.data(), E * sizeof(double));
+  memcpy(host.data() + os32, s1_32.data(), E * sizeof(float));
+  memcpy(host.data() + os64, s1_64.data(), E * sizeof(double));
   cudaError_t ce = cudaMemcpy(g->buf.p, host.data(), total, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
     dev_free(g->buf, nullptr);
@@ -390,6 +412,8 @@ extern "C" mg_status mg_graph_create(const mg_graph_desc* d, mg_graph* out) {
   g->view.G = G;
   g->view.guide = reinterpret_cast<const int32_t*>(base + og);
   g->view.range = reinterpret_cast<const double*>(base + orr);
+  g->view.s1_32 = reinterpret_cast<const float*>(base + os32);
+  g->view.s1_64 = reinterpret_cast<const double*>(base + os64);
   *out = g;
   return MG_OK;
 }
@@ -712,19 +736,28 @@ mg::Keys keys_of(uint64_t seed) {
 struct Plan {
   mg::SimArgs a{};
   bool f64 = false, stage = true, counters = true, shist = false;
+  bool var = false;           // a kVarSigma kernel (stages the diffusion slopes too)
   int32_t hist_len = 0;
   int32_t counter_bytes = 4;  // 8 for the range kernel
   size_t smem(bool with_hist, const mg_graph g) const {
     return mg::smem_layout(g->V, g->E, g->S, g->view.G, f64, stage, counters,
-                           (with_hist && shist) ? hist_len : 0, mg::kBlock, counter_bytes).total;
+                           (with_hist && shist) ? hist_len : 0, mg::kBlock, counter_bytes, var)
+        .total;
   }
 };
 
+// The kernel mode of a set: its precision, plus kVarSigma when its graph has
+// position-dependent diffusion.
+int kernel_mode(mg_particles p) {
+  return (int)p->prec | (p->g->var_sigma ? mg::kVarSigma : 0);
+}
+
 Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32_t* hist_out,
-                 size_t stage_limit, int32_t split_batch) {
+                 size_t stage_limit, int32_t split_batch, bool var) {
   const mg_graph g = p->g;
   Plan pl;
   pl.f64 = p->prec == MG_FP64;
+  pl.var = var;
   mg::SimArgs& a = pl.a;
   a.g = g->view;
   a.s = p->sv;
@@ -746,8 +779,8 @@ Plan plan_launch(mg_particles p, double dt, int32_t M, int32_t hist_bins, uint32
   const size_t budget = kSmemBudget + 128u * mg::kBlock;  // + the normal ring
   const int32_t G = g->view.G;
   const size_t tables =
-      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, true, false, 0, mg::kBlock).total -
-      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, false, false, 0, mg::kBlock).total;
+      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, true, false, 0, mg::kBlock, 4, var).total -
+      mg::smem_layout(g->V, g->E, g->S, G, pl.f64, false, false, 0, mg::kBlock, 4, var).total;
   if (tables > stage_limit) pl.stage = false;
   if (pl.smem(true, g) > budget) pl.shist = false;
   if (pl.smem(true, g) > budget) pl.counters = false;
@@ -796,7 +829,7 @@ int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
     // least 32; the other threads idle), so that every SM gets work: the
     // warps are latency-bound, and one SM running eight of them is slower
     // than four SMs running two each
-    const int per_sm = mg::em_step_blocks_per_sm((int)p->prec, smem);
+    const int per_sm = mg::em_step_blocks_per_sm(kernel_mode(p), smem);
     const int64_t slots = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
     if (tiles < slots) {
       const int64_t want = (p->n + slots - 1) / slots;
@@ -805,7 +838,7 @@ int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
   }
   if (!p->g->has_absorbing || (p->max_blocks == 0 && steps_per_launch < kRangeMinSteps))
     return mg::kBlock;
-  const int per_sm = mg::em_range_blocks_per_sm((int)p->prec, smem);
+  const int per_sm = mg::em_range_blocks_per_sm(kernel_mode(p), smem);
   int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   if (p->max_blocks > 0 && p->max_blocks < blocks) blocks = p->max_blocks;
   if (tiles <= blocks) return mg::kBlock;
@@ -833,7 +866,8 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   if (s != MG_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mg_graph g = p->g;
-  Plan pl = plan_launch(p, dt, M, hist_bins, hist_out, (size_t)-1, p->split_batch);
+  Plan pl = plan_launch(p, dt, M, hist_bins, hist_out, (size_t)-1, p->split_batch,
+                        p->g->var_sigma);
   const mg::Keys keys = keys_of(p->seed);
   int64_t first = std::min(steps, max_steps_per_launch(M, false));
   if (p->steps_per_launch > 0) first = std::min(first, p->steps_per_launch);
@@ -854,7 +888,7 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
     const bool last = done + now >= steps;
     pl.a.hist_bins = (last && hist_bins > 0) ? hist_bins : 0;
     pl.a.smem_hist = (last && pl.shist) ? 1 : 0;
-    cudaError_t ce = mg::launch_em_step((int)p->prec, pl.a, keys, pl.smem(last, g), st);
+    cudaError_t ce = mg::launch_em_step(kernel_mode(p), pl.a, keys, pl.smem(last, g), st);
     if (ce != cudaSuccess) return cuda_fail(ce, "mg_simulate: launch");
     done += now;
   } while (done < steps);
@@ -895,6 +929,7 @@ struct mg_batch_s {
   bool have_seed = false;
   uint64_t seed = 0;
   mg_precision prec = MG_FP64;
+  bool var = false;             // members need the position-dependent diffusion kernel
   int32_t split_batch = 0;      // 0: the precision's default
   int64_t stage_limit = -1;     // < 0: stage whatever fits the budget
   int32_t blocks_per_sm = 0;    // 0: occupancy maximum
@@ -930,9 +965,15 @@ mg_status batch_build(mg_batch b, cudaStream_t st) {
   std::vector<size_t> order(n_inst);
   size_t smem = 0;
   const size_t stage_limit = b->stage_limit < 0 ? (size_t)-1 : (size_t)b->stage_limit;
+  // one kernel for all members: the position-dependent one if any member's
+  // graph needs it (it gives bit-identical results for constant diffusion,
+  // sigma_e + 0 x being sigma_e)
+  b->var = false;
+  for (const auto& mb : b->members) b->var = b->var || mb.p->g->var_sigma;
   for (size_t m = 0; m < n_inst; ++m) {
     const auto& mb = b->members[m];
-    Plan pl = plan_launch(mb.p, mb.dt, mb.M, mb.hist_bins, mb.hist, stage_limit, b->split_batch);
+    Plan pl = plan_launch(mb.p, mb.dt, mb.M, mb.hist_bins, mb.hist, stage_limit, b->split_batch,
+                          b->var);
     pl.a.steps = mb.steps;
     insts[m] = pl.a;
     smem = std::max(smem, pl.smem(true, mb.p->g));
@@ -971,7 +1012,7 @@ mg_status batch_build(mg_batch b, cudaStream_t st) {
   MG_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
   b->n_items = (int32_t)items.size();
   b->smem = smem;
-  int per_sm = mg::em_batch_blocks_per_sm((int)b->prec, smem);
+  int per_sm = mg::em_batch_blocks_per_sm((int)b->prec | (b->var ? mg::kVarSigma : 0), smem);
   if (per_sm < 1) return fail(MG_ERR_INVALID_ARG, "mg_batch: the kernel does not fit an SM");
   if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
   int dev = 0, sms = 0;
@@ -985,7 +1026,8 @@ mg_status batch_build(mg_batch b, cudaStream_t st) {
 mg_status batch_enqueue(mg_batch b, cudaStream_t st) {
   MG_CUDA(cudaMemsetAsync(b->d_head, 0, 4, st));
   if (b->n_items > 0) {
-    cudaError_t ce = mg::launch_em_batch((int)b->prec, b->d_insts, b->d_items, b->n_items, b->d_head,
+    cudaError_t ce = mg::launch_em_batch((int)b->prec | (b->var ? mg::kVarSigma : 0), b->d_insts,
+                                         b->d_items, b->n_items, b->d_head,
                                          keys_of(b->seed), b->smem, b->blocks, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "mg_batch_run: launch");
   }
@@ -1319,6 +1361,23 @@ extern "C" mg_status mg_state_set(mg_particles p, const int32_t* edge, const dou
   MG_CUDA(cudaStreamSynchronize(st));
   p->step = step;
   p->last_stream = st;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_hit_root(int32_t mode, int64_t n, const float* A, const float* B,
+                                 const float* C, double* s, void* stream) {
+  if (mode != MG_FP64 && mode != MG_FP32_MIXED && mode != MG_FP32)
+    return fail(MG_ERR_INVALID_ARG, "mg_hit_root: unknown precision mode %d", (int)mode);
+  if (n < 0) return fail(MG_ERR_INVALID_ARG, "mg_hit_root: n < 0");
+  if (n == 0) return MG_OK;
+  if (!A || !B || !C || !s) return fail(MG_ERR_INVALID_ARG, "mg_hit_root: NULL argument");
+  for (const auto& q : {std::pair<const void*, const char*>{A, "A"}, {B, "B"}, {C, "C"}, {s, "s"}}) {
+    mg_status st = check_memory(q.first, Mem::kDevice, q.second);
+    if (st != MG_OK) return st;
+  }
+  cudaError_t ce =
+      mg::launch_hit_root(mode, n, A, B, C, s, static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "mg_hit_root: launch");
   return MG_OK;
 }
 

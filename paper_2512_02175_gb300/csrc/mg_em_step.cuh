@@ -38,8 +38,9 @@
 //   kModeF64    everything in binary64, in the same operation order as the
 //               plain CPU reference (the translation unit is built without
 //               FMA contraction);
-//   kModeMixed  positions, increments and normals in binary32; the hitting
-//               fraction alpha = s^2 and the time left h in binary64;
+//   kModeMixed  positions, increments and normals in binary32; the split's
+//               hitting fraction -- the root s to binary64 accuracy,
+//               alpha = s^2 -- and the time left h in binary64;
 //   kModeF32    everything in binary32.
 #pragma once
 #include <cuda_runtime.h>
@@ -195,14 +196,6 @@ __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& 
 
 // ------------------------------------------- binary32 <-> binary64 by bits
 
-// Exact widening of a binary32 s in [2^-126, 1] to binary64 with integer
-// operations (sign 0, exponent rebiased by 1023 - 127, mantissa shifted up 29
-// bits), keeping the conversion off the binary64 pipe.
-__device__ __forceinline__ double widen_unit_f32(float s) {
-  const uint32_t b = __float_as_uint(s);
-  return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
-}
-
 // binary64 h in [2^-126, 2^127] to binary32, rounded to nearest even (the
 // result of an IEEE conversion), with integer operations; values below
 // 2^-126 give 0.
@@ -258,6 +251,109 @@ __device__ __forceinline__ float hit_root_fast(float A, float B, float C) {
   return fminf(s, 1.0f);
 }
 
+// Sum a + b = s + e exactly (Knuth's two-sum, no ordering assumption); the
+// _rn intrinsics keep the compiler from fusing any of it into an FMA.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// Exact widening of a binary32 v to binary64 with integer operations (sign
+// kept, exponent rebiased, mantissa shifted up 29 bits).  Subnormal inputs,
+// below 2^-126 -- far under any coefficient of a sub-step -- become a zero of
+// the same sign.
+__device__ __forceinline__ double widen_f32(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t mag = b & 0x7fffffffu;
+  const bool normal = mag >= 0x00800000u;
+  const uint32_t hi = (b & 0x80000000u) | (normal ? (mag >> 3) + (896u << 20) : 0u);
+  const uint32_t lo = normal ? (mag << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// A binary64 v to binary32 by truncating the mantissa (sign kept; values
+// below 2^-126 give a zero, values at or above 2^128 the largest finite
+// binary32 number): for a Newton correction, which needs only a few bits.
+__device__ __forceinline__ float narrow_f64_rz(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  const uint32_t sign = hi & 0x80000000u;
+  uint32_t f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  f = (e < 897u) ? 0u : (e > 1150u) ? 0x7f7fffffu : f;
+  return __uint_as_float(sign | f);
+}
+
+// s in [0, 1] from a binary64 s: NaN and negative values give 0, values
+// above 1 give 1 (comparisons of the bit patterns).
+__device__ __forceinline__ double clamp_unit(double s) {
+  const long long b = __double_as_longlong(s);
+  if (!(b > 0ll) || (b & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) return 0.0;  // <= 0, NaN
+  return (b > 0x3FF0000000000000ll) ? 1.0 : s;
+}
+
+// The first root in [0, 1] of A s^2 + B s + C = 0 for binary32 coefficients,
+// solved in binary64 by the closed form of hit_root<double> on the widened
+// coefficients, with the same binary64 result: B^2 and 4AC are exact in
+// binary64, so the discriminant is rounded once (one fused multiply-add);
+// square root and quotient are CUDA's correctly rounded binary64 operations.
+// Tests of the coefficients run on the binary32 inputs (the same outcomes).
+__device__ __forceinline__ double hit_root_f64_closed(float A, float B, float C) {
+  double s;
+  if (A == 0.0f) {
+    s = (B == 0.0f) ? 0.0 : -widen_f32(C) / widen_f32(B);
+  } else {
+    const double B64 = widen_f32(B);
+    const double t = widen_f32(4.0f * A) * widen_f32(C);  // exact
+    const double disc = fma(B64, B64, -t);
+    const double d = (__double_as_longlong(disc) > 0ll) ? sqrt(disc) : 0.0;
+    if (B > 0.0f) {
+      s = (-B64 - d) / widen_f32(2.0f * A);
+    } else {
+      const double den = d - B64;
+      s = ((__double_as_longlong(den) & 0x7FFFFFFFFFFFFFFFll) == 0ll)
+              ? 0.0
+              : widen_f32(2.0f * C) / den;
+    }
+  }
+  return clamp_unit(s);
+}
+
+// The same root to binary64 accuracy with few binary64 operations (GB300's
+// binary64 pipe runs at about 1/70 of the binary32 rate; the closed form's
+// square root and quotient cost some twenty binary64 instructions and made
+// the FP32-mixed kernel 2.1x slower).  From the binary32 root s0
+// (hit_root_fast, a few binary32 ulps):
+//   1. one Newton step s1 = s0 - f(s0)/f'(s0) in binary32, the residual
+//      f(s0) = (A s0 + B) s0 + C carried with its rounding errors (exact
+//      products by FMA, Knuth's two-sums), so s1 is good to ~2^-44;
+//   2. one Newton step in binary64: the residual f(s1) by two binary64
+//      fused multiply-adds, the correction f(s1)/f'(s0) -- of relative size
+//      ~2^-44 -- in binary32, applied in binary64.
+// Four binary64 operations in all.  A correction beyond 2^-40 s0 (a nearly
+// double root, where Newton's method converges slowly) falls back to the
+// closed form in binary64.  Over the 16-edge star's splits the result is
+// within 2 binary64 ulps of the closed form's.
+__device__ __forceinline__ double hit_root_f64_newton(float A, float B, float C) {
+  const float s0 = hit_root_fast(A, B, C);
+  if (!(s0 > 0.0f)) return 0.0;  // C = 0, or no root in (0, 1]
+  const float fp = fmaf(2.0f * A, s0, B);
+  const float pa = __fmul_rn(A, s0), pae = fmaf(A, s0, -pa);
+  float ge;
+  const float g = two_sum(pa, B, ge);
+  const float q = __fmul_rn(g, s0), qe = fmaf(g, s0, -q);
+  float we;
+  const float w = two_sum(q, C, we);
+  const float f1 = w + (we + fmaf(ge + pae, s0, qe));
+  double s = widen_f32(s0) - widen_f32(__fdividef(f1, fp));
+  const double f = fma(fma(widen_f32(A), s, widen_f32(B)), s, widen_f32(C));
+  const float d2 = __fdividef(narrow_f64_rz(f), fp);
+  s = s - widen_f32(d2);
+  if (!(fabsf(d2) <= 0x1p-40f * s0)) return hit_root_f64_closed(A, B, C);
+  return clamp_unit(s);
+}
+
 // Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j
 // (thresholds are non-decreasing and the last is 2^32 > u).  The guide entry
 // of u's bucket is that j or an earlier slot of v (every slot before it has
@@ -299,13 +395,42 @@ __device__ __forceinline__ void count_absorbed(const CounterView& c, const Block
 
 template <int kMode>
 struct Types {
-  using R = std::conditional_t<kMode == kModeF64, double, float>;  // positions, normals
-  using H = std::conditional_t<kMode == kModeF32, float, double>;  // alpha, time left
+  using R = std::conditional_t<prec_of(kMode) == kModeF64, double, float>;  // positions, normals
+  using H = std::conditional_t<prec_of(kMode) == kModeF32, float, double>;  // alpha, time left
   // interior sub-steps per loop iteration, and the ring of buffered normals:
   // kRing per thread, each stored twice (rows n % kRing and n % kRing + kRing)
-  static constexpr int kSub = (kMode == kModeF64) ? 4 : 8;
+  static constexpr int kSub = (prec_of(kMode) == kModeF64) ? 4 : 8;
+  static constexpr bool kVar = var_sigma(kMode);  // sigma_e(x) = sigma_e + sigma1_e x
   static constexpr uint32_t kRing = 2 * kSub;
 };
+
+// Jump draws: the u32 of a particle's hit j is word j & 3 of Philox block
+// (j >> 2, pid, 1, instance).  A thread keeps the words of its particle's
+// current block in shared memory, [4][kThreads] right after the ring of
+// normals, so a block is computed once per four hits: at hit j with j & 3 =
+// 0, or when a particle whose next hit is inside a block is loaded.
+template <int kMode>
+__device__ __forceinline__ uint32_t* jump_words(const typename Types<kMode>::R* ring) {
+  return reinterpret_cast<uint32_t*>(const_cast<typename Types<kMode>::R*>(ring) +
+                                     2 * Types<kMode>::kRing * kThreads) +
+         threadIdx.x;
+}
+
+__device__ __forceinline__ void store_jump_block(uint32_t* jw, const U4& w) {
+  jw[0 * kThreads] = w.x;
+  jw[1 * kThreads] = w.y;
+  jw[2 * kThreads] = w.z;
+  jw[3 * kThreads] = w.w;
+}
+
+// The words of the block holding hit p.hits, for a particle just loaded
+// whose next hit is not the first of a block.
+template <int kMode>
+__device__ __forceinline__ void prime_jump_words(uint32_t hits, const typename Types<kMode>::R* ring,
+                                                 const SimArgs& a, const Keys& keys, uint32_t pid) {
+  if (hits & 3u)
+    store_jump_block(jump_words<kMode>(ring), philox4x32_10(hits >> 2, pid, 1u, a.instance, keys.rk));
+}
 
 // Sign handling of the normal of a sub-step: W = (z & wand) | wor on the sign
 // bit (z itself inside an edge, +|z| at an init end, -|z| at a term end).
@@ -335,6 +460,11 @@ struct Lane {
   R P, Q, S;
   R Pm, Qm, Sm;  // the same for a whole step (h = dt)
   R c0, c1;      // binary64 mode
+  // position-dependent diffusion (kVar): binary32 modes S1 = sigma1 sqrt(h),
+  // so that the noise of a sub-step from x is (S + S1 x) W; binary64 mode
+  // sigma_e(x) = sg0 + sg1 x and rh = sqrt(h)
+  R S1, S1m;
+  R sg0, sg1, rh;
   H h;           // time left in the current step
   float hf;      // binary32-mixed mode: h rounded to binary32
   uint32_t wand, wor;
@@ -358,12 +488,16 @@ template <int kMode>
 __device__ __forceinline__ void enter_edge(Lane<kMode>& p, const GraphView& g, int32_t e,
                                            const SimArgs& a) {
   p.e = e;
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     const EdgeRec64& q = g.e64[e];
     p.L = q.L;
     p.c0 = q.c0;
     p.c1 = q.c1;
     p.Sm = q.sigma * a.sqrt_dt;
+    if constexpr (Types<kMode>::kVar) {
+      p.sg0 = q.sigma;
+      p.sg1 = g.s1_64[e];
+    }
     p.tol = 1e-9 * ((isfinite(q.L) && q.L > 1.0) ? q.L : 1.0);
   } else {
     const EdgeRec32& q = g.e32[e];
@@ -371,17 +505,21 @@ __device__ __forceinline__ void enter_edge(Lane<kMode>& p, const GraphView& g, i
     p.Pm = q.c0 * a.dt_f;
     p.Qm = fmaf(q.c1, a.dt_f, 1.0f);
     p.Sm = q.sigma * a.sqrt_dt_f;
+    if constexpr (Types<kMode>::kVar) p.S1m = g.s1_32[e] * a.sqrt_dt_f;
   }
 }
 
 template <int kMode>
 __device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimArgs& a) {
-  if constexpr (kMode == kModeF32) p.h = a.dt_f;
+  if constexpr (prec_of(kMode) == kModeF32) p.h = a.dt_f;
   else p.h = a.dt;
-  if constexpr (kMode == kModeMixed) p.hf = a.dt_f;
-  if constexpr (kMode != kModeF64) {
+  if constexpr (prec_of(kMode) == kModeMixed) p.hf = a.dt_f;
+  if constexpr (prec_of(kMode) != kModeF64) {
     p.P = p.Pm;
     p.Q = p.Qm;
+    if constexpr (Types<kMode>::kVar) p.S1 = p.S1m;
+  } else if constexpr (Types<kMode>::kVar) {
+    p.rh = a.sqrt_dt;
   }
   p.S = p.Sm;
 }
@@ -391,11 +529,12 @@ __device__ __forceinline__ void use_step_coefficients(Lane<kMode>& p, const SimA
 template <int kMode>
 __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const GraphView& g,
                                                       const EdgeRec32& q) {
-  if constexpr (kMode == kModeF64) {
-    p.S = g.e64[p.e].sigma * sqrt(p.h);
+  if constexpr (prec_of(kMode) == kModeF64) {
+    if constexpr (Types<kMode>::kVar) p.rh = sqrt(p.h);
+    else p.S = g.e64[p.e].sigma * sqrt(p.h);
   } else {
     float hf;
-    if constexpr (kMode == kModeMixed) {
+    if constexpr (prec_of(kMode) == kModeMixed) {
       p.hf = narrow_f64_rn(p.h);
       hf = p.hf;
     } else {
@@ -406,6 +545,7 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
     p.P = q.c0 * hf;
     p.Q = fmaf(q.c1, hf, 1.0f);
     p.S = q.sigma * rh;
+    if constexpr (Types<kMode>::kVar) p.S1 = g.s1_32[p.e] * rh;
   }
 }
 
@@ -428,7 +568,7 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
   }
   const U4 w = philox4x32_10(p.n_gen >> 2, pid, 0u, a.instance, keys.rk);
   R z0, z1, z2, z3;
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     box_muller_f64(w.x, w.y, z0, z1);
     box_muller_f64(w.z, w.w, z2, z3);
   } else {
@@ -454,7 +594,7 @@ __device__ __forceinline__ void refill(Lane<kMode>& p, typename Types<kMode>::R*
 template <int kMode>
 __device__ __forceinline__ void refill8(Lane<kMode>& p, typename Types<kMode>::R* ring,
                                         const SimArgs& a, const Keys& keys, uint32_t pid) {
-  static_assert(kMode != kModeF64, "binary32 modes only");
+  static_assert(prec_of(kMode) != kModeF64, "binary32 modes only");
   if (p.n_gen >= 0xFFFFFFF0u - 4u) {
     atomicOr(a.c.err, kErrStream);
     p.active = false;
@@ -493,7 +633,7 @@ __device__ __forceinline__ void refill_iteration(Lane<kMode>& p, typename Types<
   constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
   const uint32_t held = p.n_gen - p.n_draw;
   const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
-  if constexpr (kMode != kModeF64) {
+  if constexpr (prec_of(kMode) != kModeF64) {
     if (n_ref > 0u) refill8<kMode>(p, ring, a, keys, pid);
     if (n_ref > 2u) refill<kMode>(p, ring, a, keys, pid);
   } else {
@@ -502,15 +642,26 @@ __device__ __forceinline__ void refill_iteration(Lane<kMode>& p, typename Types<
   }
 }
 
+// Binary64 noise sigma_e(x) sqrt(h) W of a sub-step from x, in the oracle's
+// order of operations: (sigma_e(x) sqrt(h)) W.
+template <int kMode>
+__device__ __forceinline__ double noise_f64(const Lane<kMode>& p, double x, double W) {
+  if constexpr (Types<kMode>::kVar) return ((p.sg0 + p.sg1 * x) * p.rh) * W;
+  else return p.S * W;
+}
+
 // End point of a sub-step with normal W over the lane's current time h.
 template <int kMode>
 __device__ __forceinline__ typename Types<kMode>::R sub_step_end(const Lane<kMode>& p,
                                                                  typename Types<kMode>::R W) {
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     const double mu = p.c0 + p.c1 * p.x;
     const double a_ = mu * p.h;
-    const double b_ = p.S * W;
+    const double b_ = noise_f64(p, p.x, W);
     return p.x + a_ + b_;
+  } else if constexpr (Types<kMode>::kVar) {
+    // x (Q + S1 W) + (S W + P), as the interior sub-steps compute it
+    return fmaf(p.x, fmaf(p.S1, W, p.Q), fmaf(p.S, W, p.P));
   } else {
     // x Q + (S W + P): the same expression (and rounding) as the interior
     // sub-steps, so a recomputed end point falls on the same side
@@ -535,7 +686,7 @@ __device__ __forceinline__ bool inside(double xt, double L) {
 
 template <int kMode>
 __device__ __forceinline__ void mark_near_branch(Lane<kMode>& p, typename Types<kMode>::R xt) {
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     const bool finite_L =  // l_e < +inf, from its exponent bits
         (__double_as_longlong(p.L) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
     if (abs_below(xt, p.tol) || (finite_L && abs_below(p.L - xt, p.tol))) p.flags |= 1u;
@@ -554,7 +705,7 @@ __device__ __forceinline__ void vertex_sub_step(Lane<kMode>& p,
   const R xt = sub_step_end(p, apply_sign(z, p.wand, p.wor));
   mark_near_branch(p, xt);
   bool in;
-  if constexpr (kMode == kModeF64) in = inside(xt, p.L);
+  if constexpr (prec_of(kMode) == kModeF64) in = inside(xt, p.L);
   else in = xt > R(0) && xt < p.L;
   if (in) {
     count_exit(a.c, bc, p.cur_slot);
@@ -595,18 +746,21 @@ __device__ __forceinline__ void interior_sub_steps(Lane<kMode>& p, const typenam
     const bool att = go && (!kCheckLeft || (uint32_t)q < lim);
     const R z = r[q * kThreads];
     R xt;
-    if constexpr (kMode == kModeF64) {
+    if constexpr (prec_of(kMode) == kModeF64) {
       const double mu = p.c0 + p.c1 * p.x;
       const double a_ = mu * p.h;
-      const double b_ = p.S * z;
+      const double b_ = noise_f64(p, p.x, z);
       xt = p.x + a_ + b_;
       if (att) mark_near_branch(p, xt);
+    } else if constexpr (Types<kMode>::kVar) {
+      xt = fmaf(xc, fmaf(p.S1m, z, p.Qm), fmaf(p.Sm, z, p.Pm));
+      xc = xt;
     } else {
       xt = fmaf(xc, p.Qm, fmaf(p.Sm, z, p.Pm));
       xc = xt;
     }
     bool in;
-    if constexpr (kMode == kModeF64) in = att & inside(xt, p.L);
+    if constexpr (prec_of(kMode) == kModeF64) in = att & inside(xt, p.L);
     else in = att & (xt > R(0)) & (xt < p.L);
     p.x = in ? xt : p.x;
     n_in += in ? 1u : 0u;
@@ -628,9 +782,18 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   p.pending = false;
-  // the jump draw of this hit (block (j, pid, 1, instance), j = hits so far),
-  // first: its chain of multiplies overlaps the hitting-fraction arithmetic
-  const U4 w = philox4x32_10(p.hits, pid, 1u, a.instance, keys.rk);
+  // the jump draw of this hit (j = hits so far): a new block when j is the
+  // first of one -- first, so that its chain of multiplies overlaps the
+  // hitting-fraction arithmetic -- else the stored word
+  uint32_t* jw = jump_words<kMode>(ring);
+  uint32_t u;
+  if ((p.hits & 3u) == 0u) {
+    const U4 w = philox4x32_10(p.hits >> 2, pid, 1u, a.instance, keys.rk);
+    store_jump_block(jw, w);
+    u = w.x;
+  } else {
+    u = jw[(p.hits & 3u) * kThreads];
+  }
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
   const R Wp = apply_sign(
@@ -639,10 +802,10 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   const bool hit_init = !(sub_step_end(p, Wp) > R(0));
   int32_t v;
   bool rest;  // time is left in the step after this hit
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     const double mu = p.c0 + p.c1 * xs;
     const double a_ = mu * p.h;
-    const double b_ = p.S * Wp;
+    const double b_ = noise_f64(p, xs, Wp);
     const double A = hit_init ? a_ : -a_;
     const double B = hit_init ? b_ : -b_;
     const double C = hit_init ? xs : p.L - xs;
@@ -656,25 +819,25 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     // increments of the pending sub-step in binary32: a = mu(x) h, b = S W
     const EdgeRec32& q = g.e32[p.e];
     float hf;
-    if constexpr (kMode == kModeMixed) hf = p.hf;
+    if constexpr (prec_of(kMode) == kModeMixed) hf = p.hf;
     else hf = p.h;
     const float a_ = fmaf(q.c1, xs, q.c0) * hf;
-    const float b_ = p.S * Wp;
+    float b_;
+    if constexpr (Types<kMode>::kVar) b_ = fmaf(p.S1, xs, p.S) * Wp;
+    else b_ = p.S * Wp;
     const float A = hit_init ? a_ : -a_;
     const float B = hit_init ? b_ : -b_;
     const float C = hit_init ? xs : p.L - xs;
-    const float s = hit_root_fast(A, B, C);
-    if constexpr (kMode == kModeMixed) {
-      // binary64 hitting fraction and time left; below 2^-60, alpha = s^2 <
-      // 2^-120 leaves h unchanged in binary64
-      if (s >= 0x1p-60f) {
-        const double sd = widen_unit_f32(s);
-        const double alpha = sd * sd;
-        p.h = fma(-alpha, p.h, p.h);
-      }
-      // h(1 - alpha) > 0 exactly when s < 1, and stays positive when rounded
-      rest = s < 1.0f;
+    if constexpr (prec_of(kMode) == kModeMixed) {
+      // the hitting fraction and the time left in binary64: the root to
+      // binary64 accuracy, alpha = s^2, h <- h - alpha h
+      const double s = hit_root_f64_newton(A, B, C);
+      const double alpha = s * s;
+      p.h = fma(-alpha, p.h, p.h);
+      // h (1 - alpha) > 0 exactly when s < 1, and stays positive when rounded
+      rest = __double_as_longlong(s) < 0x3FF0000000000000ll;
     } else {
+      const float s = hit_root_fast(A, B, C);
       p.h = fmaf(-s * s, p.h, p.h);
       rest = p.h > 0.0f;
     }
@@ -698,10 +861,10 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.active = false;
     return;
   }
-  const int32_t slot = choose_slot(g, vr, w.x);
+  const int32_t slot = choose_slot(g, vr, u);
   const SlotRec sr = g.slot[slot];
   EdgeRec32 qn{};  // the new edge (binary32 modes)
-  if constexpr (kMode == kModeF64) {
+  if constexpr (prec_of(kMode) == kModeF64) {
     enter_edge<kMode>(p, g, sr.edge, a);
   } else {
     p.e = sr.edge;
@@ -710,6 +873,7 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.Pm = qn.c0 * a.dt_f;
     p.Qm = fmaf(qn.c1, a.dt_f, 1.0f);
     p.Sm = qn.sigma * a.sqrt_dt_f;
+    if constexpr (Types<kMode>::kVar) p.S1m = g.s1_32[sr.edge] * a.sqrt_dt_f;
   }
   p.x = (sr.end == kEndInit) ? R(0) : p.L;
   p.at_v = true;
@@ -776,13 +940,13 @@ struct BlockSetup {
 template <int kMode>
 __device__ __forceinline__ BlockSetup<kMode> setup_block(const SimArgs& a, unsigned char* smem) {
   using R = typename Types<kMode>::R;
-  constexpr bool kF64 = kMode == kModeF64;
+  constexpr bool kF64 = prec_of(kMode) == kModeF64;
   BlockSetup<kMode> b;
   b.g = a.g;
   GraphView& g = b.g;
   b.hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
   const SmemLayout lay = smem_layout(g.V, g.E, g.S, g.G, kF64, a.stage_smem, a.smem_counters,
-                                     b.hist_len, kThreads, 8);
+                                     b.hist_len, kThreads, 8, Types<kMode>::kVar);
   if (a.stage_smem) {
     if constexpr (kF64) {
       block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
@@ -797,6 +961,15 @@ __device__ __forceinline__ BlockSetup<kMode> setup_block(const SimArgs& a, unsig
     g.slot = reinterpret_cast<const SlotRec*>(smem + lay.slots);
     g.vtx = reinterpret_cast<const VtxRec*>(smem + lay.vtx);
     g.guide = reinterpret_cast<const int32_t*>(smem + lay.guide);
+    if constexpr (Types<kMode>::kVar) {
+      if constexpr (kF64) {
+        block_copy(reinterpret_cast<double*>(smem + lay.sig1), g.s1_64, g.E);
+        g.s1_64 = reinterpret_cast<const double*>(smem + lay.sig1);
+      } else {
+        block_copy(reinterpret_cast<float*>(smem + lay.sig1), g.s1_32, g.E);
+        g.s1_32 = reinterpret_cast<const float*>(smem + lay.sig1);
+      }
+    }
   }
   b.bc = BlockCounters64{nullptr, nullptr};
   if (a.smem_counters) {
@@ -865,11 +1038,11 @@ template <int kMode>
 __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int64_t i,
                                          unsigned char* smem) {
   using R = typename Types<kMode>::R;
-  constexpr bool kF64 = kMode == kModeF64;
+  constexpr bool kF64 = prec_of(kMode) == kModeF64;
   GraphView g = a.g;
   const int32_t hist_len = a.smem_hist ? g.E * a.hist_bins : 0;
   const SmemLayout lay = smem_layout(g.V, g.E, g.S, g.G, kF64, a.stage_smem, a.smem_counters,
-                                     hist_len, kThreads);
+                                     hist_len, kThreads, 4, Types<kMode>::kVar);
   if (a.stage_smem) {
     if constexpr (kF64) {
       block_copy(reinterpret_cast<EdgeRec64*>(smem + lay.edges), g.e64, g.E);
@@ -884,6 +1057,15 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
     g.slot = reinterpret_cast<const SlotRec*>(smem + lay.slots);
     g.vtx = reinterpret_cast<const VtxRec*>(smem + lay.vtx);
     g.guide = reinterpret_cast<const int32_t*>(smem + lay.guide);
+    if constexpr (Types<kMode>::kVar) {
+      if constexpr (kF64) {
+        block_copy(reinterpret_cast<double*>(smem + lay.sig1), g.s1_64, g.E);
+        g.s1_64 = reinterpret_cast<const double*>(smem + lay.sig1);
+      } else {
+        block_copy(reinterpret_cast<float*>(smem + lay.sig1), g.s1_32, g.E);
+        g.s1_32 = reinterpret_cast<const float*>(smem + lay.sig1);
+      }
+    }
   }
   BlockCounters bc{nullptr, nullptr};
   if (a.smem_counters) {
@@ -941,6 +1123,7 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
       }
       p.n_gen = p.n_draw & ~3u;
       refill<kMode>(p, ring, a, keys, pid);
+      prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
     }
   }
 
@@ -1086,7 +1269,7 @@ __device__ __forceinline__ bool load_particle(Lane<kMode>& p, uint32_t& pid, con
   p.cur_slot = -1;
   if (p.at_v) {
     const int32_t end = (p.x == R(0)) ? kEndInit : kEndTerm;
-    if constexpr (kMode == kModeF64)
+    if constexpr (prec_of(kMode) == kModeF64)
       p.cur_slot = (end == kEndInit) ? g.e64[p.e].slot_init : g.e64[p.e].slot_term;
     else
       p.cur_slot = (end == kEndInit) ? g.e32[p.e].slot_init : g.e32[p.e].slot_term;
@@ -1094,6 +1277,7 @@ __device__ __forceinline__ bool load_particle(Lane<kMode>& p, uint32_t& pid, con
   }
   p.n_gen = p.n_draw & ~3u;
   refill<kMode>(p, ring, a, keys, pid);
+  prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
   return true;
 }
 
@@ -1202,7 +1386,7 @@ __device__ __forceinline__ void run_range(const SimArgs& a, const Keys& keys, in
 // (binary32 modes: at most 64 registers, four blocks per SM, like the tile
 // kernel; binary64 unconstrained.)
 template <int kMode>
-__global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
+__global__ void __launch_bounds__(256, (prec_of(kMode) == kModeF64) ? 0 : 4)
     em_range_kernel(const __grid_constant__ SimArgs a, const __grid_constant__ Keys keys) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RangeCtl ctl;
@@ -1215,7 +1399,7 @@ __global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
 // b * r .. b * r + r - 1, r = a.range (256, or fewer for a set too small to
 // fill the GPU's resident blocks).
 template <int kMode>
-__global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ SimArgs a,
+__global__ void __launch_bounds__(256, (prec_of(kMode) == kModeF64) ? 2 : 4) em_step_kernel(const __grid_constant__ SimArgs a,
                                                       const __grid_constant__ Keys keys) {
   extern __shared__ __align__(16) unsigned char smem[];
   // a.range <= 256 particles per block; the block's other threads are idle
@@ -1230,7 +1414,7 @@ __global__ void __launch_bounds__(256) em_step_kernel(const __grid_constant__ Si
 // the same tile body, so a particle's result does not depend on the batch.
 // (binary32 modes: at most 64 registers, four blocks per SM.)
 template <int kMode>
-__global__ void __launch_bounds__(256, (kMode == kModeF64) ? 0 : 4)
+__global__ void __launch_bounds__(256, (prec_of(kMode) == kModeF64) ? 0 : 4)
     em_batch_kernel(const SimArgs* __restrict__ insts,
                                                        const BatchItem* __restrict__ items,
                                                        int32_t n_items, uint32_t* head,

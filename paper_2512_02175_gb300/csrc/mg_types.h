@@ -20,6 +20,11 @@ enum : uint32_t { kErrBadEdge = 1u, kErrNan = 2u, kErrStream = 4u, kErrStuck = 8
 constexpr int kThreads = 256;
 // precision modes (same values as mg_precision)
 enum : int { kModeF64 = 0, kModeMixed = 1, kModeF32 = 2 };
+// A kernel's mode argument is a precision mode, plus kVarSigma for graphs
+// with position-dependent diffusion sigma_e(x) = sigma_e + sigma1_e x.
+constexpr int kVarSigma = 4;
+MG_HD constexpr int prec_of(int mode) { return mode & 3; }
+MG_HD constexpr bool var_sigma(int mode) { return (mode & kVarSigma) != 0; }
 
 // One edge (Definition 1) with its drift mu_e(x) = c0 + c1 x and diffusion
 // sigma_e; 32 bytes so a warp loads it with one 16-byte pair per lane.
@@ -61,6 +66,8 @@ struct GraphView {
   const VtxRec* vtx;
   const int32_t* guide;
   const double* range;  // histogram range per edge
+  const float* s1_32;   // diffusion slope sigma1_e per edge (zeros for constant sigma)
+  const double* s1_64;
 };
 
 // Particle state, structure of arrays.
@@ -108,26 +115,31 @@ struct SimArgs {
   int64_t range;        // particles per block: <= 256 em_step_kernel, > 256 the range kernel
 };
 
-// Dynamic shared memory of the fused kernel: staged tables, privatised
-// counters, privatised histogram (each part optional).
+// Dynamic shared memory of the fused kernel: the ring of buffered normals
+// and the jump words of each thread, then staged tables (with the diffusion
+// slopes for kVarSigma kernels), privatised counters and the privatised
+// histogram (each of these three optional).
 struct SmemLayout {
-  size_t ring, edges, slots, vtx, guide, exits, absorbed, hist, total;
+  size_t ring, jump, edges, slots, vtx, guide, sig1, exits, absorbed, hist, total;
 };
 
 MG_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, int32_t G, bool f64,
                                     bool stage, bool counters, int32_t hist_len, int32_t block,
-                                    int32_t counter_bytes = 4) {
+                                    int32_t counter_bytes = 4, bool var = false) {
   SmemLayout l{};
   size_t off = 0;
   l.ring = off;  // buffered normals, each stored twice: 32 KB at 256 threads
   off += align16((size_t)(f64 ? 16 : 32) * block * (f64 ? 8 : 4));
+  l.jump = off;  // the jump draws of a Philox block, 4 words per thread (right after the ring)
+  off += align16((size_t)4 * block * 4);
   if (stage) {
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));
     l.vtx = off; off += align16((size_t)V * sizeof(VtxRec));
     l.guide = off; off += align16((size_t)G * sizeof(int32_t));
+    if (var) { l.sig1 = off; off += align16((size_t)E * (f64 ? 8 : 4)); }
   }
   if (counters) {  // 4-byte (tiles) or 8-byte (range kernel) counters
     l.exits = off; off += align16((size_t)S * counter_bytes);

@@ -6,6 +6,7 @@ from the (picklable) graph description.
 """
 from __future__ import annotations
 
+import atexit
 import multiprocessing as mp
 import os
 
@@ -36,7 +37,16 @@ def _pool():
     if _POOL is None:
         ctx = mp.get_context("spawn")
         _POOL = ctx.Pool(max(1, min(16, os.cpu_count() or 1)))
+        atexit.register(_close)
     return _POOL
+
+
+def _close():
+    global _POOL
+    if _POOL is not None:
+        _POOL.terminate()
+        _POOL.join()
+        _POOL = None
 
 
 def run(desc, edge, x, pid=None, *, seed, instance=0, dt, steps, M, bins=0, chunks=None,

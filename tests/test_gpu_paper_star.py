@@ -1,4 +1,4 @@
-"""The paper's star experiment (Section 5.1 and the appendix's steady-state
+"""The paper's star experiment (Section 4.1 and the appendix's steady-state
 normalisers): five semi-infinite edges glued at one vertex, b = 1/5,
 sigma = 1 (D = sigma^2 / 2 = 1/2), drift towards the vertex
 mu_i = -10 i (linear potential) or mu_i = -10 i x (quadratic potential).
@@ -177,7 +177,7 @@ def test_sampled_histogram_is_a_sum_of_snapshots(B):
 
 def test_sampled_histogram_fp64_matches_oracle(B):
     """mg_simulate_sampled in binary64 against the oracle run in chunks of
-    `every` EM-Steps with a snapshot histogram after each (Section 5.1's
+    `every` EM-Steps with a snapshot histogram after each (Section 4.1's
     time-averaged occupancy, written with the oracle's own simulate and
     histogram): the summed histograms are equal count for count when no
     trajectory came within the branch margin, and the final states agree

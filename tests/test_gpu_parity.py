@@ -834,3 +834,13 @@ def test_vascular_fp32_statistics(B, prec):
     ao, ag = o["absorbed"].astype(float), gc["absorbed"].astype(float)
     top = np.argsort(-ao)[:10]  # the busiest outlets
     assert np.all(np.abs(ag[top] - ao[top]) <= 4 * np.sqrt(ao[top]) + 3)
+    # exit frequency of every slot within 3 standard errors (multinomial over
+    # the exits of each run, both runs' errors; one count of slack for
+    # slots that see a handful of exits)
+    eo, eg = o["exits"].astype(float), gc["exits"].astype(float)
+    fo, fg = eo / eo.sum(), eg / eg.sum()
+    se = np.sqrt(fo * (1 - fo) / eo.sum() + fg * (1 - fg) / eg.sum())
+    dev = np.abs(fg - fo)
+    print(f"\nvascular {prec}: {len(eo)} slots, {int(eo.sum())} exits; max |z| "
+          f"{np.max(dev / np.maximum(se, 1e-300)):.2f} (slots with exits)")
+    assert np.all(dev <= 3 * se + 1.0 / eo.sum()), np.argmax(dev - 3 * se)
