@@ -65,6 +65,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hist", action="store_true",
                     help="time the EM-Steps without the fused histogram tail")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="star16_langevin: skip the FP32, FP64 and served sub-measurements "
+                         "the default line carries")
+    ap.add_argument("--full", action="store_true",
+                    help="served: the configured request sizes (n = 2^U[14,24]) over a 10-s "
+                         "Poisson window instead of the reduced trace")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batch512: scale every instance's particle count by this factor")
     ap.add_argument("--cpu-sample", type=int, default=16_384)
@@ -86,8 +92,10 @@ def config(args, world):
             "n_particles_per_gpu": args.n, "global_particles": args.n * world,
             "dt": DT, "em_steps_per_step": args.em_steps, "M": M,
             "hist_bins_per_edge": 0 if args.no_hist else BINS,
-            "precision": {"mixed": "fp32 with fp64 hitting fraction and time left",
-                          "fp32": "fp32", "fp64": "fp64"}[args.precision],
+            "precision": {"mixed": "fp32 positions, increments and normals; the split's "
+                                   "hitting fraction (root to binary64 accuracy, alpha = s^2) "
+                                   "and time left in fp64",
+                          "fp32": "fp32 throughout", "fp64": "fp64 throughout"}[args.precision],
             "parallelism": f"particle shards x{world}",
             "l2": f"state {28 if args.precision == 'fp64' else 24} B/particle x N > L2 (129 MB): "
                   "no flush needed"}
@@ -239,6 +247,58 @@ def kernel_hash():
     return h.hexdigest()
 
 
+def time_precision(B, torch, g, e0, x0, precision, em_steps, steps, warmup, stream):
+    """Particle-steps/s of `steps` launches of `em_steps` EM-Steps of the
+    benchmark's workload (fused histogram) in another precision mode, timed
+    like the headline (CUDA events on the launch stream, resident state)."""
+    p = B.Particles(g, e0, x0, seed=SEED, precision=_mode(B, precision), stream=stream)
+    hist = torch.zeros(g.n_edges * BINS, dtype=torch.int32, device="cuda")
+
+    def step():
+        hist.zero_()
+        p.simulate(DT, em_steps, M, BINS, hist, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    c0 = p.counts(stream)["particle_steps"]
+    ev = _events(torch, steps)
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            step()
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ps = p.counts(stream)["particle_steps"] - c0
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    p.close()
+    return {"value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
+            "ms_per_launch": statistics.mean(ms), "em_steps_per_launch": em_steps,
+            "launches": steps, "warmup": warmup, "n_particles": len(e0)}
+
+
+def sub_measurements(args, B, torch, g, e0, x0, stream):
+    """The metric's other parts, measured in the same run: the FP32 and FP64
+    modes on the same workload (FP64 at 10^3 EM-Steps per launch), and the
+    served trace (continuous batching, FP32-mixed and FP64, against the plain
+    one-launch-per-request FP64 path)."""
+    out = {}
+    fp32 = time_precision(B, torch, g, e0, x0, "fp32", args.em_steps, 3, 2, stream)
+    out["fp32"] = fp32
+    fp64 = time_precision(B, torch, g, e0, x0, "fp64", 1000, 2, 1, stream)
+    prof = _profile(kernel_hash(), "em_step_star16_fp64.md")
+    fp64["roofline"] = {"bound": "fp64", "unit": "FP64-pipe busy fraction",
+                        "frac": float(prof["fp64-pipe-active-pct"]) / 100.0 if prof else None,
+                        "source": "ncu capture of the binary64 kernel "
+                                  "(profiles/em_step_star16_fp64.md), while its source hash "
+                                  "matches"}
+    out["fp64"] = fp64
+    torch.cuda.synchronize()
+    out["served"] = served_trace(B, torch, full=False)
+    return out
+
+
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -369,6 +429,9 @@ def run_ours(args):
                          f"per core"}
     counts = p.counts(stream)
     p.close()
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras = sub_measurements(args, B, torch, g, e0, x0, stream)
     g.close()
     if rank == 0:
         out = {
@@ -382,6 +445,7 @@ def run_ours(args):
             "launch_ms": launch_ms,
             "truncations": counts["truncations"],
         }
+        out.update(extras)
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -587,42 +651,85 @@ def run_batch512(args):
     return 0
 
 
-def run_served(args):
-    """A Poisson request stream (200 requests/s over 3 s) over the 3-edge
-    Brownian star, the 16-edge Langevin star and the vascular network; n =
-    2^U[12,18], steps log-U[100, 5000], dt log-U[1e-4, 1e-2].  The continuous-
-    batching server (binary32-mixed, 2 streams, rounds of max(500 steps,
-    2^27 particle-steps) per member, 32 GB admission budget) against the plain
-    path: each request alone as one FP64 mg_simulate, in arrival order."""
-    import torch
-    from paper_2512_02175_gb300 import binding as B
+SERVED_GRAPHS = None
+
+
+def served_trace(B, torch, full=False, precisions=("mixed", "fp64")):
+    """A Poisson request stream (200 requests/s) over the 3-edge Brownian
+    star, the 16-edge Langevin star and the vascular network; steps
+    log-U[100, 5000], dt log-U[1e-4, 1e-2]; n = 2^U[12,18] over 3 s (the
+    reduced trace), or with ``full`` the configured n = 2^U[14,24] over 10 s
+    (about 6e11 particle-steps offered per second, more than one GPU
+    serves).  The continuous-batching server (2 streams, rounds of max(500
+    steps, 2^27 particle-steps) per member, 32 GB admission budget) in each
+    of ``precisions``, then the plain path -- each request alone as one FP64
+    mg_simulate, in arrival order -- on the same trace.  A run is cut off
+    after 120 s (full) or 600 s: unanswered requests count as latencies
+    beyond the cut (their percentiles are then reported as lower bounds)."""
     from paper_2512_02175_gb300 import serve
-    B.load()
-    B.use_torch_allocator()
     graphs = {"star3": W.star_brownian(3), "star16": W.star_langevin(16),
               "vascular": W.vascular()}
-    trace = lambda: serve.poisson_trace(200.0, 3.0, 17, graphs, n_range=(12, 18),
+    rate, window, n_range, limit = (200.0, 10.0, (14, 24), 120.0) if full else \
+        (200.0, 3.0, (12, 18), 600.0)
+    trace = lambda: serve.poisson_trace(rate, window, 17, graphs, n_range=n_range,
                                          init=serve.default_init)
-    be = serve.GpuBackend(graphs, _mode(B, args.precision), seed=SEED, n_lanes=2)
-    srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500, round_work=1 << 27)
-    # warm-up: a short trace (allocator, module load, graph capture paths)
-    warm = serve.poisson_trace(200.0, 0.2, 99, graphs, n_range=(10, 12), init=serve.default_init)
-    srv.run_trace(warm)
-    srv.results = []
-    torch.cuda.synchronize()
-    res = srv.run_trace(trace())
-    served = serve.latency_summary(res)
-    be.close()
-    plain = serve.latency_summary(serve.serve_plain(trace(), graphs, B.MG_FP64, seed=SEED))
-    out = {"metric": METRIC, "value": served["served_particle_steps_per_s"],
+    reqs = trace()
+    offered = sum(r.n * r.steps for r in reqs)
+    out = {"trace": {"rate_per_s": rate, "window_s": window, "requests": len(reqs),
+                     "n_range_log2": list(n_range), "steps_range": [100, 5000],
+                     "dt_range": [1e-4, 1e-2], "offered_particle_steps_per_s": offered / window,
+                     "cut_off_s": limit, "lanes": 2, "chunk_steps": 500,
+                     "round_work": 1 << 27}}
+
+    def summary(results, t_run):
+        s = serve.latency_summary(results)
+        ok = [r for r in results if r.error is None]
+        s["answered"] = len(ok)
+        s["wall_s"] = t_run
+        if len(ok) < len(reqs):  # open requests waited at least until the cut
+            lat = np.array([r.latency for r in ok] + [np.inf] * (len(reqs) - len(ok)))
+            for q, key in ((50, "p50_s"), (99, "p99_s")):
+                v = float(np.percentile(lat, q))
+                s[key] = v if np.isfinite(v) else None
+                if not np.isfinite(v):
+                    s[key + "_at_least"] = limit - window
+        return s
+
+    for prec in precisions:
+        be = serve.GpuBackend(graphs, _mode(B, prec), seed=SEED, n_lanes=2)
+        srv = serve.Server(be, mem_budget=32 << 30, n_lanes=2, chunk_steps=500,
+                           round_work=1 << 27)
+        warm = serve.poisson_trace(200.0, 0.2, 99, graphs, n_range=(10, 12),
+                                   init=serve.default_init)
+        srv.run_trace(warm)
+        srv.results = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = srv.run_trace(trace(), time_limit=limit, partial=True)
+        out[f"served_{prec}"] = summary(res, time.perf_counter() - t0)
+        be.close()
+        torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = serve.serve_plain(trace(), graphs, B.MG_FP64, seed=SEED, time_limit=limit)
+    out["plain_fp64"] = summary(plain, time.perf_counter() - t0)
+    return out
+
+
+def run_served(args):
+    """The served configuration alone (see served_trace): its line reports the
+    FP32-mixed served throughput as ``value``, every served and plain
+    summary beside it."""
+    import torch
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    B.use_torch_allocator()
+    res = served_trace(B, torch, full=args.full)
+    out = {"metric": METRIC, "value": res["served_mixed"]["served_particle_steps_per_s"],
            "unit": "particle-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-           "config": {"workload": "served", "rate_per_s": 200, "window_s": 3.0,
-                      "n_range_log2": [12, 18], "steps_range": [100, 5000],
-                      "dt_range": [1e-4, 1e-2], "precision": args.precision,
-                      "lanes": 2, "chunk_steps": 500, "round_work": 1 << 27},
-           "served": served, "plain_fp64_per_request": plain}
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "served_full" if args.full else "served", **res["trace"]},
+           **{k: v for k, v in res.items() if k != "trace"}}
     print(json.dumps(out))
     return 0
 

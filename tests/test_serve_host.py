@@ -230,3 +230,31 @@ def test_zero_step_request_completes_at_admission():
         srv.step()
     assert srv.idle() and sorted(r.rid for r in srv.results) == [0, 1]
     assert all(rid != 0 for tok in be.launches for rid, _ in tok["members"])
+
+
+def test_trace_cut_off_abandons_open_requests():
+    """A trace cut off at its time limit (partial=True) returns the answered
+    requests, releases every admitted one and leaves nothing queued; without
+    partial it raises."""
+    be = FakeBackend(delay_polls=3)
+    clk = FakeClock()
+
+    class TickingServer(serve.Server):
+        def step(self):
+            clk.t += 1.0  # every pass costs a second of the fake clock
+            return super().step()
+
+    reqs = _reqs(30, seed=4)
+    for q in reqs:
+        q.arrival = 0.0
+    srv = TickingServer(be, mem_budget=60_000, n_lanes=2, chunk_steps=200, clock=clk)
+    res = srv.run_trace(reqs, time_limit=300.0, poll=0.0, partial=True)
+    assert 0 < len(res) < len(reqs)
+    assert srv.idle() and srv.reserved == 0 and not be.live
+    assert all(l is None for l in srv.lanes)
+    srv2 = TickingServer(FakeBackend(delay_polls=3), mem_budget=60_000, n_lanes=2,
+                         chunk_steps=200, clock=clk)
+    for q in reqs:
+        q.arrival = 0.0
+    with pytest.raises(TimeoutError):
+        srv2.run_trace(reqs, time_limit=40.0, poll=0.0)
