@@ -9,8 +9,13 @@
 // hands the library a custom allocator which is not safe to call from every
 // place a histogram is read.  This entry point stages the counts in a
 // file-scope device array instead, of fixed size: at most kMaxStaticBins
-// counts (n_edges x bins), 4 MiB, held by every GPU that loads the library
-// until the process exits.
+// counts (n_edges x bins), 4 MiB, held by every GPU that loads the library's
+// device code until the process exits.  Under CUDA's lazy module loading that
+// code (and the array) is loaded on a device by the first kernel or symbol
+// lookup there, which can synchronise: the first call on a device belongs in
+// set-up.  The array's device address is looked up once per device and kept;
+// cudaDeviceReset frees the array, so a caller that resets a device must not
+// call this entry point on it again in the same process.
 #include <cuda_runtime.h>
 
 #include <cstdio>

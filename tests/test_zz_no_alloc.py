@@ -42,3 +42,38 @@ def test_static_histogram_equals_allocating_one(prec):
     assert ei.value.status == B.MG_ERR_INVALID_ARG
     p.close()
     g.close()
+
+
+def test_static_histogram_allocates_nothing():
+    """The defining property: with the library on cudaMalloc, repeated calls
+    on a set that never had a histogram leave the device's free memory
+    unchanged, while the allocating entry point, on another such set, takes
+    its 4 MiB staging buffer (the check can see an allocation)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2512_02175_gb300 import binding as B
+    B.load()
+    B.use_cuda_allocator()
+    d = W.star_langevin(16)
+    e, x = W.uniform_on_edges(d, 100_000, 3)
+    g = B.Graph(d)
+    bins = (1 << 20) // 16  # the largest request: 2^20 counts, 4 MiB
+    warm = B.Particles(g, e, x, seed=2, precision=1)
+    out = np.zeros(16 * bins, np.uint32)
+    B.mg_histogram_static(warm.h, bins, out)  # first call on the device: set-up
+    fresh = B.Particles(g, e, x, seed=2, precision=1)
+    other = B.Particles(g, e, x, seed=2, precision=1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        B.mg_histogram_static(fresh.h, bins, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert out.sum() == 100_000
+    ref = other.histogram(bins)  # allocates its staging buffer
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free0
+    assert np.array_equal(ref, out)
+    for p in (warm, fresh, other):
+        p.close()
+    g.close()
