@@ -480,6 +480,8 @@ def run_vascular(args):
     g = B.Graph(d)
     de, dx = torch.from_numpy(e0).cuda(), torch.from_numpy(x0).cuda()
     p = B.Particles(g, de, dx, seed=SEED, precision=_mode(B, args.precision), stream=stream)
+    if args.split_batch:
+        p.set_tuning(split_batch=args.split_batch)
     hist = torch.zeros(g.n_edges * bins, dtype=torch.int32, device="cuda")
 
     def step():
@@ -540,6 +542,8 @@ def run_star3(args):
     g = B.Graph(d)
     de, dx = torch.from_numpy(e0).cuda(), torch.from_numpy(x0).cuda()
     p = B.Particles(g, de, dx, seed=0, precision=_mode(B, prec), stream=stream)
+    if args.split_batch:
+        p.set_tuning(split_batch=args.split_batch)
     hist = torch.zeros(g.n_edges * bins, dtype=torch.int32, device="cuda")
 
     def step():
@@ -696,9 +700,9 @@ def served_trace(B, torch, full=False, precisions=None):
         s["answered"] = len(ok)
         s["wall_s"] = t_run
         if len(ok) < len(reqs):  # open requests waited at least until the cut
-            lat = np.array([r.latency for r in ok] + [np.inf] * (len(reqs) - len(ok)))
+            lat = np.sort([r.latency for r in ok] + [np.inf] * (len(reqs) - len(ok)))
             for q, key in ((50, "p50_s"), (99, "p99_s")):
-                v = float(np.percentile(lat, q))
+                v = float(lat[max(0, math.ceil(q / 100 * len(lat)) - 1)])  # nearest rank
                 s[key] = v if np.isfinite(v) else None
                 if not np.isfinite(v):
                     s[key + "_at_least"] = limit - window

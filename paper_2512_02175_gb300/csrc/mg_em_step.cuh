@@ -405,10 +405,14 @@ struct Types {
 };
 
 // Jump draws: the u32 of a particle's hit j is word j & 3 of Philox block
-// (j >> 2, pid, 1, instance).  A thread keeps the words of its particle's
-// current block in shared memory, [4][kThreads] right after the ring of
-// normals, so a block is computed once per four hits: at hit j with j & 3 =
-// 0, or when a particle whose next hit is inside a block is loaded.
+// (j >> 2, pid, 1, instance).  A thread keeps two blocks of its particle's
+// words in shared memory, [8][kThreads] right after the ring of normals
+// (block b in rows 4 (b & 1) .. 4 (b & 1) + 3, so hit j reads row j & 7);
+// jtop is the first hit whose word is not there yet.  Blocks are computed
+// ahead of the hits, warp-wide, in the refill phase -- whenever a lane of the
+// warp has used up its words, every lane with room for a block computes its
+// next one, so one Philox evaluation serves many lanes -- and only inside a
+// split pass when a chain of hits outruns that.
 template <int kMode>
 __device__ __forceinline__ uint32_t* jump_words(const typename Types<kMode>::R* ring) {
   return reinterpret_cast<uint32_t*>(const_cast<typename Types<kMode>::R*>(ring) +
@@ -416,20 +420,24 @@ __device__ __forceinline__ uint32_t* jump_words(const typename Types<kMode>::R* 
          threadIdx.x;
 }
 
-__device__ __forceinline__ void store_jump_block(uint32_t* jw, const U4& w) {
-  jw[0 * kThreads] = w.x;
-  jw[1 * kThreads] = w.y;
-  jw[2 * kThreads] = w.z;
-  jw[3 * kThreads] = w.w;
+// Stores the words of block b (its slot b & 1).
+__device__ __forceinline__ void store_jump_block(uint32_t* jw, uint32_t b, const U4& w) {
+  uint32_t* r = jw + (b & 1u) * 4u * kThreads;
+  r[0 * kThreads] = w.x;
+  r[1 * kThreads] = w.y;
+  r[2 * kThreads] = w.z;
+  r[3 * kThreads] = w.w;
 }
 
-// The words of the block holding hit p.hits, for a particle just loaded
-// whose next hit is not the first of a block.
+// A particle just loaded: the block holding its next hit.
 template <int kMode>
-__device__ __forceinline__ void prime_jump_words(uint32_t hits, const typename Types<kMode>::R* ring,
-                                                 const SimArgs& a, const Keys& keys, uint32_t pid) {
-  if (hits & 3u)
-    store_jump_block(jump_words<kMode>(ring), philox4x32_10(hits >> 2, pid, 1u, a.instance, keys.rk));
+__device__ __forceinline__ uint32_t prime_jump_words(uint32_t hits,
+                                                     const typename Types<kMode>::R* ring,
+                                                     const SimArgs& a, const Keys& keys,
+                                                     uint32_t pid) {
+  store_jump_block(jump_words<kMode>(ring), hits >> 2,
+                   philox4x32_10(hits >> 2, pid, 1u, a.instance, keys.rk));
+  return (hits & ~3u) + 4u;
 }
 
 // Sign handling of the normal of a sub-step: W = (z & wand) | wor on the sign
@@ -451,6 +459,7 @@ struct Lane {
   int32_t e;
   R x;
   uint32_t n_draw, n_gen, hits, first_hits, flags;
+  uint32_t jtop;  // first hit whose jump word is not in shared memory yet
   // current edge
   R L;
   R tol;  // binary64 mode: branch margin 1e-9 max(1, l_e)
@@ -630,6 +639,14 @@ template <int kMode>
 __device__ __forceinline__ void refill_iteration(Lane<kMode>& p, typename Types<kMode>::R* ring,
                                                  const SimArgs& a, const Keys& keys,
                                                  uint32_t pid) {
+  // jump words: when a lane of the warp has none left, every lane with a
+  // used-up slot computes its next block (the warp evaluates Philox once)
+  if (__any_sync(0xffffffffu, p.active && p.hits >= p.jtop) && p.active &&
+      p.jtop - p.hits <= 4u) {
+    store_jump_block(jump_words<kMode>(ring), p.jtop >> 2,
+                     philox4x32_10(p.jtop >> 2, pid, 1u, a.instance, keys.rk));
+    p.jtop += 4u;
+  }
   constexpr uint32_t kSub = (uint32_t)Types<kMode>::kSub;
   const uint32_t held = p.n_gen - p.n_draw;
   const uint32_t n_ref = (p.active && !p.pending && held <= kSub) ? (kSub + 4u - held) >> 2 : 0u;
@@ -782,17 +799,18 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   p.pending = false;
-  // the jump draw of this hit (j = hits so far): a new block when j is the
-  // first of one -- first, so that its chain of multiplies overlaps the
-  // hitting-fraction arithmetic -- else the stored word
+  // the jump draw of this hit (j = hits so far): the stored word, or -- a
+  // chain of hits that used up the stored blocks -- a new block (j is then
+  // the first hit of it)
   uint32_t* jw = jump_words<kMode>(ring);
   uint32_t u;
-  if ((p.hits & 3u) == 0u) {
+  if (p.hits >= p.jtop) {
     const U4 w = philox4x32_10(p.hits >> 2, pid, 1u, a.instance, keys.rk);
-    store_jump_block(jw, w);
+    store_jump_block(jw, p.hits >> 2, w);
+    p.jtop = p.hits + 4u;
     u = w.x;
   } else {
-    u = jw[(p.hits & 3u) * kThreads];
+    u = jw[(p.hits & 7u) * kThreads];
   }
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
@@ -800,7 +818,14 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
       ring[((p.n_draw - 1u) & (Types<kMode>::kRing - 1u)) * kThreads + threadIdx.x], p.wand,
       p.wor);
   const bool hit_init = !(sub_step_end(p, Wp) > R(0));
+  // the hit vertex and its record first: the load's latency (a round trip to
+  // L2 for graphs whose tables stay out of shared memory) overlaps the
+  // hitting-fraction arithmetic below; v < 0 (the far end of a semi-infinite
+  // edge, reached only by an overflow) reads vertex 0 and is reported below
   int32_t v;
+  if constexpr (prec_of(kMode) == kModeF64) v = hit_init ? g.e64[p.e].src : g.e64[p.e].dst;
+  else v = hit_init ? g.e32[p.e].src : g.e32[p.e].dst;
+  const VtxRec vr = g.vtx[v < 0 ? 0 : v];
   bool rest;  // time is left in the step after this hit
   if constexpr (prec_of(kMode) == kModeF64) {
     const double mu = p.c0 + p.c1 * xs;
@@ -814,7 +839,6 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.h = (1.0 - alpha) * p.h;
     if (p.h < 1e-9 * a.dt) p.flags |= 1u;
     rest = p.h > 0.0;
-    v = hit_init ? g.e64[p.e].src : g.e64[p.e].dst;
   } else {
     // increments of the pending sub-step in binary32: a = mu(x) h, b = S W
     const EdgeRec32& q = g.e32[p.e];
@@ -841,7 +865,6 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
       p.h = fmaf(-s * s, p.h, p.h);
       rest = p.h > 0.0f;
     }
-    v = hit_init ? q.src : q.dst;
   }
   const uint32_t j = p.hits;
   p.hits = j + 1u;
@@ -854,7 +877,6 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     p.active = false;
     return;
   }
-  const VtxRec vr = g.vtx[v];
   if (vr.kind == kVertexAbsorbing) {
     count_absorbed(a.c, bc, v);
     p.e = kDead;
@@ -1123,7 +1145,7 @@ __device__ __forceinline__ void run_tile(const SimArgs& a, const Keys& keys, int
       }
       p.n_gen = p.n_draw & ~3u;
       refill<kMode>(p, ring, a, keys, pid);
-      prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
+      p.jtop = prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
     }
   }
 
@@ -1277,7 +1299,7 @@ __device__ __forceinline__ bool load_particle(Lane<kMode>& p, uint32_t& pid, con
   }
   p.n_gen = p.n_draw & ~3u;
   refill<kMode>(p, ring, a, keys, pid);
-  prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
+  p.jtop = prime_jump_words<kMode>(p.hits, ring, a, keys, pid);
   return true;
 }
 

@@ -132,8 +132,8 @@ MG_HD inline SmemLayout smem_layout(int32_t V, int32_t E, int32_t S, int32_t G, 
   size_t off = 0;
   l.ring = off;  // buffered normals, each stored twice: 32 KB at 256 threads
   off += align16((size_t)(f64 ? 16 : 32) * block * (f64 ? 8 : 4));
-  l.jump = off;  // the jump draws of a Philox block, 4 words per thread (right after the ring)
-  off += align16((size_t)4 * block * 4);
+  l.jump = off;  // the jump draws of two Philox blocks, 8 words per thread (right after the ring)
+  off += align16((size_t)8 * block * 4);
   if (stage) {
     l.edges = off; off += align16((size_t)E * (f64 ? sizeof(EdgeRec64) : sizeof(EdgeRec32)));
     l.slots = off; off += align16((size_t)S * sizeof(SlotRec));
