@@ -17,7 +17,7 @@ import threading
 from dataclasses import dataclass
 
 DEFAULT_CANDIDATES = dict(
-    split_batch=(1, 2, 4),
+    split_batch=(1, 2, 4, 6),
     stage_limit_bytes=(0, 16 * 1024, -1),
     blocks_per_sm=(0, 3),
 )

@@ -704,15 +704,19 @@ extern "C" mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch
 
 namespace {
 
-// Default number of pending lanes that triggers a batched split pass.  With
-// eight interior sub-steps per loop iteration the pending lanes of one
-// iteration already form the batch; waiting for more costs more than it saves
-// (measured on the 16-edge Langevin star: 1 and 2 best, 8 about 20% slower).
+// Default number of pending lanes that triggers a batched split pass (a
+// warp also resolves its pending lanes whenever no other lane can move).  A
+// pass costs about the same whatever number of lanes it resolves, while a
+// pending lane idles until it runs, so the best batch grows with the cost of
+// a split.  Measured on the 16-edge Langevin star (2^24 particles, one GB300,
+// particle-steps/s): FP32-mixed, whose binary64 root makes splits dear,
+// 3.48e11 at 1, 3.72 at 4, 3.74 at 5, 3.70 at 6, 3.47 at 8; FP32 4.42e11 at
+// 1, 4.49 at 3, 4.40 at 5; FP64 8.62e9 at 1, 8.74 at 2, 8.07 at 4.
 int32_t default_split_batch(mg_precision prec) {
   switch (prec) {
-    case MG_FP32: return 1;
-    case MG_FP32_MIXED: return 1;
-    default: return 1;
+    case MG_FP32: return 3;
+    case MG_FP32_MIXED: return 5;
+    default: return 2;
   }
 }
 

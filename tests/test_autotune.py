@@ -15,7 +15,7 @@ def test_search_picks_fastest_and_caches(tmp_path):
     best = A.tune("k", trial, path=path)
     assert best == A.Tuning(2, 16384, 3)
     n = len(calls)
-    assert n == 3 * 3 * 2
+    assert n == len(A.DEFAULT_CANDIDATES["split_batch"]) * 3 * 2
     again = A.tune("k", trial, path=path)  # from the cache: no new trials
     assert again == best and len(calls) == n
     fresh = A.tune("k", trial, path=path, refresh=True)
