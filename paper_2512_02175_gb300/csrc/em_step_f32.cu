@@ -205,7 +205,7 @@ __global__ void hit_root_kernel(int32_t mode, int64_t n, const float* __restrict
     if (mode == kModeF32) {
       r = widen_f32(hit_root_fast(a, b, c));
     } else if (mode == kModeMixed) {
-      r = hit_root_f64_newton(a, b, c);
+      r = hit_root_f64_eft(a, b, c);
     } else {
       r = hit_root_f64_closed(a, b, c);
     }

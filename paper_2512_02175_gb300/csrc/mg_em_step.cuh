@@ -320,38 +320,83 @@ __device__ __forceinline__ double hit_root_f64_closed(float A, float B, float C)
   return clamp_unit(s);
 }
 
-// The same root to binary64 accuracy with few binary64 operations (GB300's
-// binary64 pipe runs at about 1/70 of the binary32 rate; the closed form's
-// square root and quotient cost some twenty binary64 instructions and made
-// the FP32-mixed kernel 2.1x slower).  From the binary32 root s0
-// (hit_root_fast, a few binary32 ulps):
-//   1. one Newton step s1 = s0 - f(s0)/f'(s0) in binary32, the residual
-//      f(s0) = (A s0 + B) s0 + C carried with its rounding errors (exact
-//      products by FMA, Knuth's two-sums), so s1 is good to ~2^-44;
-//   2. one Newton step in binary64: the residual f(s1) by two binary64
-//      fused multiply-adds, the correction f(s1)/f'(s0) -- of relative size
-//      ~2^-44 -- in binary32, applied in binary64.
-// Four binary64 operations in all.  A correction beyond 2^-40 s0 (a nearly
-// double root, where Newton's method converges slowly) falls back to the
-// closed form in binary64.  Over the 16-edge star's splits the result is
-// within 2 binary64 ulps of the closed form's.
-__device__ __forceinline__ double hit_root_f64_newton(float A, float B, float C) {
-  const float s0 = hit_root_fast(A, B, C);
-  if (!(s0 > 0.0f)) return 0.0;  // C = 0, or no root in (0, 1]
-  const float fp = fmaf(2.0f * A, s0, B);
-  const float pa = __fmul_rn(A, s0), pae = fmaf(A, s0, -pa);
-  float ge;
-  const float g = two_sum(pa, B, ge);
-  const float q = __fmul_rn(g, s0), qe = fmaf(g, s0, -q);
-  float we;
-  const float w = two_sum(q, C, we);
-  const float f1 = w + (we + fmaf(ge + pae, s0, qe));
-  double s = widen_f32(s0) - widen_f32(__fdividef(f1, fp));
-  const double f = fma(fma(widen_f32(A), s, widen_f32(B)), s, widen_f32(C));
-  const float d2 = __fdividef(narrow_f64_rz(f), fp);
-  s = s - widen_f32(d2);
-  if (!(fabsf(d2) <= 0x1p-40f * s0)) return hit_root_f64_closed(A, B, C);
-  return clamp_unit(s);
+// Exact product a b = p + e (the FMA gives the rounding error exactly).
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+  const float p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+  return p;
+}
+
+// The same root to binary64 accuracy, refined in binary32 error-free
+// arithmetic (GB300's binary64 pipe runs at about 1/70 of the binary32 rate,
+// so the refinement keeps off it).  From the binary32 root s0:
+//   f(s0) = (A s0 + B) s0 + C is split exactly into binary32 terms (exact
+//   products by FMA, Knuth's two-sums): f0 + f0l to ~2^-70 of the terms;
+//   f'(s0) = 2 A s0 + B as d + dl;
+//   Newton step 1: t = -f0 / d (a binary32 correction of ~2^-22 s0);
+//   f(s0 + t) = f(s0) + t f'(s0) + A t^2, again to ~2^-68 of the terms
+//   (t d exactly, the rest small), so that
+//   Newton step 2: t2 = -f(s0 + t) / d leaves s = s0 + t + t2 good to
+//   ~2^-66 s0.
+// ok = false for a second correction beyond 2^-40 s0 (a nearly double root,
+// where Newton's method converges slowly): the caller falls back to the
+// closed form in binary64.  s0 = 0: no root in (0, 1], or C = 0.
+struct RootParts {
+  float s0, t, t2;
+  bool ok;
+};
+
+__device__ __forceinline__ RootParts hit_root_parts(float A, float B, float C) {
+  RootParts r{hit_root_fast(A, B, C), 0.0f, 0.0f, true};
+  const float s0 = r.s0;
+  if (!(s0 > 0.0f)) return r;
+  float pae, ge, qe, we, re, rse, a1e, a2e, f0e, de, ue, ve;
+  const float pa = two_prod(A, s0, pae);   // A s0
+  const float g = two_sum(pa, B, ge);      // A s0 + B = g + ge + pae
+  const float q = two_prod(g, s0, qe);     // g s0
+  const float w = two_sum(q, C, we);       // g s0 + C = w + we + qe
+  const float rr = two_sum(ge, pae, re);   // (ge + pae) s0 = rr s0 + re s0
+  const float rs = two_prod(rr, s0, rse);
+  const float a1 = two_sum(we, qe, a1e);
+  const float a2 = two_sum(a1, rs, a2e);
+  const float lo = ((a1e + a2e) + rse) + re * s0;
+  const float f0 = two_sum(w, a2, f0e);
+  const float f0l = f0e + lo;              // f(s0) = f0 + f0l
+  const float d = two_sum(2.0f * pa, B, de);
+  const float dl = de + 2.0f * pae;        // f'(s0) = d + dl
+  const float t = -__fdividef(f0, d);
+  const float u = two_prod(t, d, ue);
+  const float v = two_sum(f0, u, ve);
+  const float f1 = v + ((((ve + f0l) + ue) + t * dl) + A * (t * t));
+  const float t2 = -__fdividef(f1, d);
+  r.t = t;
+  r.t2 = t2;
+  r.ok = fabsf(t2) <= 0x1p-40f * s0;
+  return r;
+}
+
+// The root s in binary64: (s0 + t) exactly, then + t2 (one rounding).
+__device__ __forceinline__ double hit_root_f64_eft(float A, float B, float C) {
+  const RootParts r = hit_root_parts(A, B, C);
+  if (!(r.s0 > 0.0f)) return 0.0;
+  if (!r.ok) return hit_root_f64_closed(A, B, C);
+  return clamp_unit((widen_f32(r.s0) + widen_f32(r.t)) + widen_f32(r.t2));
+}
+
+// The hitting fraction alpha = s^2 of that root in binary64, with one
+// binary64 addition and one FMA: sa = s0 + t exactly, alpha = sa^2 + 2 sa t2
+// (t2^2 < 2^-80 s^2 is dropped, and 2 sa t2 is taken as 2 s0 t2 in binary32,
+// within 2^-20 of itself: ~2^-63 of alpha), clamped to [0, 1].
+__device__ __forceinline__ double hit_alpha_f64(float A, float B, float C) {
+  const RootParts r = hit_root_parts(A, B, C);
+  if (!(r.s0 > 0.0f)) return 0.0;
+  if (!r.ok) {
+    const double s = hit_root_f64_closed(A, B, C);
+    return s * s;
+  }
+  const double sa = widen_f32(r.s0) + widen_f32(r.t);
+  const double alpha = fma(sa, sa, widen_f32(2.0f * r.s0 * r.t2));
+  return (__double_as_longlong(alpha) > 0x3FF0000000000000ll) ? 1.0 : alpha;
 }
 
 // Slot of vertex v drawn by u: the first j in [begin, end) with u < T_j
@@ -855,11 +900,10 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
     if constexpr (prec_of(kMode) == kModeMixed) {
       // the hitting fraction and the time left in binary64: the root to
       // binary64 accuracy, alpha = s^2, h <- h - alpha h
-      const double s = hit_root_f64_newton(A, B, C);
-      const double alpha = s * s;
+      const double alpha = hit_alpha_f64(A, B, C);
       p.h = fma(-alpha, p.h, p.h);
-      // h (1 - alpha) > 0 exactly when s < 1, and stays positive when rounded
-      rest = __double_as_longlong(s) < 0x3FF0000000000000ll;
+      // h (1 - alpha) > 0 exactly when alpha < 1, and stays positive when rounded
+      rest = __double_as_longlong(alpha) < 0x3FF0000000000000ll;
     } else {
       const float s = hit_root_fast(A, B, C);
       p.h = fmaf(-s * s, p.h, p.h);

@@ -4,8 +4,10 @@ oracle's or_root, on the coefficients the binary32 modes form.
 The partial sub-step of Algorithms 1 and 2 reaches the vertex after the
 fraction alpha = s^2 of the time left, s the first root in [0, 1] of
 A s^2 + B s + C = 0.  The kernels form A, B, C in binary32; the FP32-mixed
-mode solves for s in binary64 (the precision stated for the hitting
-fraction), the FP32 mode in binary32.  Here:
+mode solves for s to binary64 accuracy (the precision stated for the hitting
+fraction: a binary32 root refined by Newton steps whose residuals are carried
+exactly in binary32 error-free arithmetic, summed in binary64), the FP32
+mode in binary32.  Here:
 
 * the FP64 mode's closed form equals or_root bit for bit (both compute the
   same binary64 operations, correctly rounded square root and quotient);
