@@ -683,8 +683,10 @@ extern "C" mg_status mg_particles_info(mg_particles p, int64_t* n, int32_t* prec
 
 namespace {
 
-// Largest dynamic shared memory the fused kernel may take per block while
-// keeping up to 8 resident blocks of 256 threads on an SM.
+// Dynamic shared memory the fused kernel may take per block beside its ring
+// of normals (32 KB): the jump words (8 KB), then staged tables, counters and
+// histogram (16 KB), so that four blocks of 256 threads -- the most the
+// registers allow -- stay resident on an SM (4 x 56 KB of its 228 KB).
 constexpr size_t kSmemBudget = 24 * 1024;
 
 }  // namespace
