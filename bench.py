@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default=None,
-                    help="default: mixed (star3_brownian: fp64, as that configuration is given)")
+                    help="default: mixed (star3_brownian: fp64; vascular and batch512: fp32 -- "
+                         "each as its configuration is given)")
     ap.add_argument("--split-batch", type=int, default=0)
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--em-steps", type=int, default=EM_STEPS)
@@ -465,7 +466,8 @@ def _events(torch, k):
 def run_vascular(args):
     """The synthetic vascular network: 2^26 tracers injected at the inlets,
     2000 EM-Steps (dt = 10x the explicit one-cell finite-volume limit), M = 32,
-    16-bin histograms; each benchmark step restarts from the injected state
+    16-bin histograms, FP32 as that configuration is given (--precision
+    overrides); each benchmark step restarts from the injected state
     (device-resident) so every step does the same work."""
     import torch
     from paper_2512_02175_gb300 import binding as B
@@ -473,13 +475,14 @@ def run_vascular(args):
     n = 1 << 26 if args.n == (1 << 24) else args.n
     steps = 2000 if args.em_steps == EM_STEPS else args.em_steps
     Mv, bins = 32, 16
+    prec = args.precision if args.precision_given else "fp32"
     e0, x0 = W.inject_at_inlets(d, n, 11)
     B.load()
     B.use_torch_allocator()
     stream = torch.cuda.Stream()
     g = B.Graph(d)
     de, dx = torch.from_numpy(e0).cuda(), torch.from_numpy(x0).cuda()
-    p = B.Particles(g, de, dx, seed=SEED, precision=_mode(B, args.precision), stream=stream)
+    p = B.Particles(g, de, dx, seed=SEED, precision=_mode(B, prec), stream=stream)
     if args.split_batch:
         p.set_tuning(split_batch=args.split_batch)
     hist = torch.zeros(g.n_edges * bins, dtype=torch.int32, device="cuda")
@@ -507,12 +510,12 @@ def run_vascular(args):
     out = {"metric": METRIC, "value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
            "data": "synthetic",
            "config": {"workload": "vascular", "vertices": int(d["n_vertices"]),
                       "edges": int(len(d["src"])), "n_particles": n, "dt_s": d["dt"],
                       "em_steps_per_step": steps, "M": Mv, "hist_bins_per_edge": bins,
-                      "precision": args.precision},
+                      "precision": prec},
            "absorbed_fraction": float(sum(c["absorbed"]) / n),
            "truncations_per_step": c["truncations"] / steps, "launch_ms": ms}
     p.close()
@@ -584,14 +587,16 @@ def run_star3(args):
 def run_batch512(args):
     """512 uneven instances (stars with 3..64 edges, random trees with
     100..10^4 edges, N ~ 2^U[12,22], 100..5000 steps) in one persistent launch,
-    replayed from a captured CUDA graph, with autotuned launch tuning."""
+    replayed from a captured CUDA graph, with autotuned launch tuning; FP32 as
+    that configuration is given (--precision fp64 for its FP64 variant)."""
     import torch
     from paper_2512_02175_gb300 import autotune as A
     from paper_2512_02175_gb300 import binding as B
     B.load()
     B.use_torch_allocator()
     insts = W.batch_instances(512, n_scale=args.scale)
-    prec = _mode(B, args.precision)
+    prec_name = args.precision if args.precision_given else "fp32"
+    prec = _mode(B, prec_name)
     graphs, parts = [], []
     for k, it in enumerate(insts):
         g = B.Graph(it["graph"])
@@ -638,12 +643,12 @@ def run_batch512(args):
     out = {"metric": METRIC, "value": ps / (sum(ms) / 1e3), "unit": "particle-steps/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else "f32",
            "data": "synthetic",
            "config": {"workload": "batch512", "instances": n_members, "work_items": n_items,
                       "persistent_blocks": blocks, "particles": int(sum(i["n"] for i in insts)),
                       "particle_steps_per_step": int(sum(i["n"] * i["steps"] for i in insts)),
-                      "cuda_graph": True, "tuning": tun.as_dict(), "precision": args.precision,
+                      "cuda_graph": True, "tuning": tun.as_dict(), "precision": prec_name,
                       "particle_scale": args.scale},
            "launch_ms": ms}
     b.close()
