@@ -47,6 +47,9 @@ DT, EM_STEPS, M, BINS, SEED = 1e-3, 10_000, 16, 32, 0
 # multiplies + 2 three-input XORs) / 4 = 10; Box-Muller per normal = 7; EM
 # update 2 FMA, interior test 2 compares + 1 branch = 5; loop control 1.
 I_ALG = 23
+# Thread-instructions per particle-step of the fast path plus the vertex
+# splits' share (the estimate 35-45; its middle)
+I_MIN = 40
 METRIC = "particle-steps/sec"
 
 
@@ -391,7 +394,10 @@ def run_ours(args):
                     "frac": achieved / peak, "traffic": _traffic(prof, n),
                     "note": f"{I_ALG} algorithmic thread-instructions per particle-step (fast "
                             f"path) x particle-steps per launch / mean launch time; peak = "
-                            f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"}
+                            f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
+                    # the same against the estimate of 35-45 instructions per
+                    # particle-step that counts the splits' share (40 taken)
+                    "frac_at_i_min_40": achieved * I_MIN / I_ALG / peak}
         if prof:  # the issue-rate view, from the committed ncu capture of this kernel
             roofline["issue_active_frac"] = float(prof["issue-active-pct"]) / 100.0
             roofline["warp_inst_per_warp_step"] = float(prof["warp-inst-per-warp-step"])
