@@ -1,7 +1,7 @@
 """The benchmark's configuration -- the 16-edge Langevin star (lengths
 U[0.5, 2], V_e = a_e (x - c_e)^2, sigma = sqrt(2), equal b, reflecting
-leaves, M = 16) in FP32-mixed -- against the FP64 oracle itself and against
-its stationary density.
+leaves, M = 16) in FP32-mixed (and, for the first comparison, FP32) --
+against the FP64 oracle itself and against its stationary density.
 
 * Against the oracle at N = 2^24 (the benchmark's launch: 10^4 EM-Steps, the
   fused 32-bin histogram): per-edge occupancy and per-slot exit frequencies
@@ -70,11 +70,13 @@ def batch_se(parts, key, norm):
     return est.std(axis=0, ddof=1) / math.sqrt(len(parts))
 
 
-def test_star16_full_size_against_oracle(B):
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_star16_full_size_against_oracle(B, prec):
     d = W.star_langevin(E)
     n = 1 << 24
     e, x = W.uniform_on_edges(d, n, 11)
-    hist, cnt, st = gpu_hist(B, d, e, x, 10_000)
+    P = {"mixed": B.MG_FP32_MIXED, "fp32": B.MG_FP32}[prec]
+    hist, cnt, st = gpu_hist(B, d, e, x, 10_000, prec=P)
     assert hist.sum() == n and cnt["particle_steps"] == n * 10_000
     ns = 1 << 18
     o = oracle_pool.run(d, e[:ns], x[:ns], seed=0, dt=DT, steps=10_000, M=M, bins=BINS,
@@ -91,10 +93,10 @@ def test_star16_full_size_against_oracle(B):
     z_exit = (fg - fo) / np.maximum(se_f, 1e-300)
     # coupled histogram of the same 2^18 particles (the GPU result of a
     # particle does not depend on the set it runs in)
-    hs, _, _ = gpu_hist(B, d, e[:ns], x[:ns], 10_000)
+    hs, _, _ = gpu_hist(B, d, e[:ns], x[:ns], 10_000, prec=P)
     tv = 0.5 * np.abs(hs - o["hist"]).sum() / ns
     floor = math.sqrt(E * BINS / (math.pi * ns))
-    print(f"\nstar16 2^24 x 10^4 FP32-mixed vs oracle 2^18: max |z| occupancy "
+    print(f"\nstar16 2^24 x 10^4 {prec} vs oracle 2^18: max |z| occupancy "
           f"{np.abs(z_occ).max():.2f}, exits {np.abs(z_exit).max():.2f}; coupled TV of 2^18 "
           f"{tv:.2e} (independent noise floor {floor:.2e})")
     assert np.all(np.abs(z_occ) <= 3), z_occ
