@@ -444,8 +444,10 @@ struct Types {
 // jtop is the first hit whose word is not there yet.  Blocks are computed
 // ahead of the hits, warp-wide, in the refill phase -- whenever a lane of the
 // warp has used up its words, every lane with room for a block computes its
-// next one, so one Philox evaluation serves many lanes -- and only inside a
-// split pass when a chain of hits outruns that.
+// next one, so one Philox evaluation serves many lanes.  A split pass takes
+// one hit per lane and a refill phase follows every pass, so a lane always
+// holds its next word when it splits; the split keeps a fallback that
+// computes the block itself should a lane ever arrive without it.
 template <int kMode>
 __device__ __forceinline__ uint32_t* jump_words(const typename Types<kMode>::R* ring) {
   return reinterpret_cast<uint32_t*>(const_cast<typename Types<kMode>::R*>(ring) +
@@ -833,8 +835,8 @@ __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const 
   using R = typename Types<kMode>::R;
   p.pending = false;
   // the jump draw of this hit (j = hits so far): the stored word, or -- a
-  // chain of hits that used up the stored blocks -- a new block (j is then
-  // the first hit of it)
+  // lane that used up its stored blocks (the fallback; j is then the first
+  // hit of the new block) -- a new block
   uint32_t* jw = jump_words<kMode>(ring);
   uint32_t u;
   if (p.hits >= p.jtop) {
@@ -1080,9 +1082,9 @@ __device__ __forceinline__ void flush_block(const SimArgs& a, const BlockSetup<k
       if (b.shist[k]) atomicAdd(&a.hist[k], b.shist[k]);
 }
 
-// One iteration of a warp after its liveness check: the split pass (each
-// pending lane's whole chain of vertex hits), the refills, the sub-step from
-// a vertex, and kSub interior sub-steps.
+// One iteration of a warp after its liveness check: the split pass (one
+// vertex hit of each pending lane and its sub-step from the vertex), the
+// refills, the sub-step from a vertex, and kSub interior sub-steps.
 template <int kMode, typename BC>
 __device__ __forceinline__ void iteration(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
                                           const Keys& keys, const BC& bc,
