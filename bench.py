@@ -535,8 +535,10 @@ def run_star3(args):
     particles round-robin on the edges, dt = 1e-3, 1000 EM-Steps, M = 8,
     32-bin histograms and the exit counts; FP64 unless --precision says
     otherwise.  Each benchmark step restarts from the device-resident start.
-    40 blocks of 256 particles cannot fill 152 SMs: the number shows what a
-    single small launch costs, not the kernel's throughput."""
+    The library spreads so small a set over the GPU's resident blocks (313
+    blocks of 32 particles on 152 SMs), which still leaves most lanes idle:
+    the number shows what a single small launch costs, not the kernel's
+    throughput."""
     import torch
     from paper_2512_02175_gb300 import binding as B
     d = W.star_brownian(3)
@@ -581,7 +583,7 @@ def run_star3(args):
            "data": "synthetic",
            "config": {"workload": "star3_brownian", "edges": 3, "n_particles": n, "dt": 1e-3,
                       "em_steps_per_step": steps, "M": M3, "hist_bins_per_edge": bins,
-                      "precision": prec, "blocks": (n + 255) // 256,
+                      "precision": prec,
                       "l2": "state below L2; each step restarts from the same start"},
            "centre_exits": [int(v) for v in c["exits"][:3]], "launch_ms": ms}
     p.close()
