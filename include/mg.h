@@ -186,9 +186,7 @@ mg_status mg_particles_destroy(mg_particles p);
  * max_blocks = for graphs with absorbing vertices, the most blocks of 256
  * threads a launch uses: a set larger than that is spread evenly over the
  * blocks, whose lanes take the next particle when theirs dies or finishes
- * (0: the library's choice -- the blocks resident on the GPU at once, for
- * launches of at least 768 EM-Steps, where enough particles die for it to
- * pay). */
+ * (0: the library's choice -- the blocks resident on the GPU at once). */
 mg_status mg_particles_set_tuning(mg_particles p, int32_t split_batch, int64_t steps_per_launch,
                                   int32_t max_blocks);
 

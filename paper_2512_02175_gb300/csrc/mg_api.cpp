@@ -812,18 +812,19 @@ int64_t max_steps_per_launch(int32_t M, bool smem_counters) {
 
 // Particles per block of mg_simulate: 256 (one per thread, em_step_kernel),
 // fewer for a set that cannot fill the GPU's resident blocks (see below),
-// unless particles can die, the set is larger than the blocks resident at
-// once (or max_blocks) and a launch is long enough for many of them to die:
-// then the set is spread evenly over those blocks and em_range_kernel's lanes
-// claim the next particle when theirs dies or finishes.  Its bookkeeping
-// (claims, global counters) costs ~10% when few particles die, repaid once
-// many die within the launch: on the synthetic vascular network (2^24
-// tracers) range / tile throughput is 0.90 at 250 EM-Steps per launch (30%
-// absorbed), 0.94 at 500, 1.03 at 1000 (65%).  An explicit max_blocks selects
-// it for any launch length.
-constexpr int64_t kRangeMinSteps = 768;
-
-int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
+// unless particles can die and the set is larger than the blocks resident at
+// once (or max_blocks): then the set is spread evenly over those blocks and
+// em_range_kernel's lanes claim the next particle when theirs dies or
+// finishes, so no lane idles beside its warp's slowest particle.  On such
+// graphs the particles' work is uneven even before many die (tracers near
+// short edges split far more often), and with one split per lane per pass
+// the range kernel is the faster at every launch length measured on the
+// synthetic vascular network (2^24 tracers, binary32): range / tile
+// throughput 1.30 at 16 EM-Steps per launch (4% absorbed), 1.21 at 128
+// (19%), 1.21 at 250, 1.26 at 500, 1.57 at 1000, 2.06 at 2000 (81%);
+// FP32-mixed 1.30 to 1.37 at 32 to 128.  An explicit max_blocks bounds its
+// block count.
+int64_t block_range(mg_particles p, size_t smem) {
   const int64_t tiles = (p->n + mg::kBlock - 1) / mg::kBlock;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -842,8 +843,7 @@ int64_t block_range(mg_particles p, size_t smem, int64_t steps_per_launch) {
       return std::min<int64_t>(mg::kBlock, std::max<int64_t>(32, (want + 31) / 32 * 32));
     }
   }
-  if (!p->g->has_absorbing || (p->max_blocks == 0 && steps_per_launch < kRangeMinSteps))
-    return mg::kBlock;
+  if (!p->g->has_absorbing) return mg::kBlock;
   const int per_sm = mg::em_range_blocks_per_sm(kernel_mode(p), smem);
   int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   if (p->max_blocks > 0 && p->max_blocks < blocks) blocks = p->max_blocks;
@@ -877,7 +877,7 @@ extern "C" mg_status mg_simulate(mg_particles p, double dt, int64_t steps, int32
   const mg::Keys keys = keys_of(p->seed);
   int64_t first = std::min(steps, max_steps_per_launch(M, false));
   if (p->steps_per_launch > 0) first = std::min(first, p->steps_per_launch);
-  pl.a.range = block_range(p, pl.smem(true, g), first);
+  pl.a.range = block_range(p, pl.smem(true, g));
   if (pl.a.range > mg::kBlock) {  // blocks run many particles: 64-bit counters
     pl.counter_bytes = 8;
     if (pl.counters && pl.smem(true, g) > kSmemBudget + 128u * mg::kBlock) {

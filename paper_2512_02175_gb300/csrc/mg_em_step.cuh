@@ -196,16 +196,15 @@ __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& 
 
 // ------------------------------------------- binary32 <-> binary64 by bits
 
-// binary64 h in [2^-126, 2^127] to binary32, rounded to nearest even (the
-// result of an IEEE conversion), with integer operations; values below
-// 2^-126 give 0.
-__device__ __forceinline__ float narrow_f64_rn(double h) {
+// binary64 h in [0, 2^128) to binary32, truncated (rounded toward zero),
+// with integer operations; values below 2^-126 give 0.  The binary32 time of
+// the FP32-mixed mode's sub-step coefficients: the binary64 h stays the time
+// left, and truncating rather than rounding to nearest saves the rounding
+// step's operations in every split (1% on the 16-edge star) at an error of
+// at most one binary32 ulp in those coefficients.
+__device__ __forceinline__ float narrow_f64_rz(double h) {
   const uint32_t hi = (uint32_t)__double2hiint(h), lo = (uint32_t)__double2loint(h);
-  const uint32_t e = (hi >> 20) & 0x7ffu;
-  uint32_t f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const uint32_t r = lo & 0x1fffffffu;  // the 29 bits rounded away
-  f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
-  return (e < 897u) ? 0.0f : __uint_as_float(f);
+  return (hi < 0x38100000u) ? 0.0f : __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
 }
 
 // ---------------------------------------------------- hitting-fraction root
@@ -446,8 +445,9 @@ struct Types {
 // warp has used up its words, every lane with room for a block computes its
 // next one, so one Philox evaluation serves many lanes.  A split pass takes
 // one hit per lane and a refill phase follows every pass, so a lane always
-// holds its next word when it splits; the split keeps a fallback that
-// computes the block itself should a lane ever arrive without it.
+// holds its next word when it splits (the split only reads it: computing a
+// missing block there as well cost 3% on the vascular network, for code that
+// never ran).
 template <int kMode>
 __device__ __forceinline__ uint32_t* jump_words(const typename Types<kMode>::R* ring) {
   return reinterpret_cast<uint32_t*>(const_cast<typename Types<kMode>::R*>(ring) +
@@ -510,7 +510,7 @@ struct Lane {
   R S1, S1m;
   R sg0, sg1, rh;
   H h;           // time left in the current step
-  float hf;      // binary32-mixed mode: h rounded to binary32
+  float hf;      // binary32-mixed mode: h truncated to binary32 (narrow_f64_rz)
   uint32_t wand, wor;
   int32_t cur_slot;  // slot of the vertex end the particle sits at
   int32_t k;         // splits in the current step
@@ -579,7 +579,7 @@ __device__ __forceinline__ void use_rest_coefficients(Lane<kMode>& p, const Grap
   } else {
     float hf;
     if constexpr (prec_of(kMode) == kModeMixed) {
-      p.hf = narrow_f64_rn(p.h);
+      p.hf = narrow_f64_rz(p.h);
       hf = p.hf;
     } else {
       hf = p.h;
@@ -829,24 +829,14 @@ __device__ __forceinline__ void interior_sub_steps(Lane<kMode>& p, const typenam
 // jump draw, next edge, and the coefficients of the rest of the step.
 template <int kMode, typename BC>
 __device__ __forceinline__ void split(Lane<kMode>& p, const GraphView& g, const SimArgs& a,
-                                      const Keys& keys, const BC& bc,
-                                      const typename Types<kMode>::R* ring, uint32_t pid,
+                                      const BC& bc, const typename Types<kMode>::R* ring,
                                       uint32_t& trunc) {
   using R = typename Types<kMode>::R;
   p.pending = false;
-  // the jump draw of this hit (j = hits so far): the stored word, or -- a
-  // lane that used up its stored blocks (the fallback; j is then the first
-  // hit of the new block) -- a new block
-  uint32_t* jw = jump_words<kMode>(ring);
-  uint32_t u;
-  if (p.hits >= p.jtop) {
-    const U4 w = philox4x32_10(p.hits >> 2, pid, 1u, a.instance, keys.rk);
-    store_jump_block(jw, p.hits >> 2, w);
-    p.jtop = p.hits + 4u;
-    u = w.x;
-  } else {
-    u = jw[(p.hits & 7u) * kThreads];
-  }
+  // the jump draw of this hit (j = hits so far), stored ahead by the refill
+  // phase; a lane without it would be a library bug, reported as such
+  if (p.hits >= p.jtop) atomicOr(a.c.err, kErrStuck);
+  const uint32_t u = jump_words<kMode>(ring)[(p.hits & 7u) * kThreads];
   const R xs = p.x;
   // the pending sub-step again: its normal is still in the ring
   const R Wp = apply_sign(
@@ -964,7 +954,7 @@ __device__ __forceinline__ void split_and_continue(Lane<kMode>& p, const GraphVi
                                                    typename Types<kMode>::R* ring, uint32_t pid,
                                                    uint32_t& trunc) {
   if (!p.pending) return;
-  split<kMode>(p, g, a, keys, bc, ring, pid, trunc);
+  split<kMode>(p, g, a, bc, ring, trunc);
   if (!p.active || !p.in_cont) return;
   if (p.n_gen == p.n_draw) {  // the split used up the buffer
     refill<kMode>(p, ring, a, keys, pid);
