@@ -111,7 +111,7 @@ def test_new_arrivals_join_next_round():
     clk = FakeClock()
     srv = serve.Server(be, mem_budget=10**9, n_lanes=1, chunk_steps=100, clock=clk)
     srv.submit(serve.Request(0, "g", 10, 1000, 1e-3))
-    srv.step()  # round 1: request 0 alone
+    srv.step()  # the first server round: request 0 alone
     srv.submit(serve.Request(1, "g", 10, 1000, 1e-3))
     for _ in range(3):
         srv.step()
