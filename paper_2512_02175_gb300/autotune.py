@@ -17,7 +17,9 @@ import threading
 from dataclasses import dataclass
 
 DEFAULT_CANDIDATES = dict(
-    split_batch=(1, 2, 4, 6),
+    # 0: the precision's own default (5 pending lanes for FP32-mixed, 3 for
+    # FP32, 2 for FP64)
+    split_batch=(0, 1, 2, 4),
     stage_limit_bytes=(0, 16 * 1024, -1),
     blocks_per_sm=(0, 3),
 )
