@@ -511,6 +511,8 @@ struct Lane {
   // current edge
   R L;
   R tol;  // binary64 mode: branch margin 1e-9 max(1, l_e)
+  // binary64 mode: bit patterns bounding the band (l_e - tol, l_e + tol)
+  long long near_lo, near_hi;
   // sub-step coefficients for the time h of the current sub-step:
   //   binary32: x~ = x Q + P + S W, P = c0 h, Q = 1 + c1 h, S = sigma sqrt(h)
   //   binary64: x~ = (x + (c0 + c1 x) h) + S W, S = sigma sqrt(h)
@@ -556,6 +558,13 @@ __device__ __forceinline__ void enter_edge(Lane<kMode>& p, const GraphView& g, i
       p.sg1 = g.s1_64[e];
     }
     p.tol = 1e-9 * ((isfinite(q.L) && q.L > 1.0) ? q.L : 1.0);
+    // the band around the terminal end as bit patterns of non-negative
+    // binary64 numbers (empty for l_e = +inf), so that the near-branch test
+    // of every sub-step is integer comparisons (the subtraction l_e - x~ it
+    // replaces ran on the binary64 pipe once per sub-step)
+    const double lo = q.L - p.tol;
+    p.near_lo = lo > 0.0 ? __double_as_longlong(lo) : 0ll;
+    p.near_hi = __double_as_longlong(q.L + p.tol);
   } else {
     const EdgeRec32& q = g.e32[e];
     p.L = q.L;
@@ -752,9 +761,10 @@ __device__ __forceinline__ bool inside(double xt, double L) {
 template <int kMode>
 __device__ __forceinline__ void mark_near_branch(Lane<kMode>& p, typename Types<kMode>::R xt) {
   if constexpr (prec_of(kMode) == kModeF64) {
-    const bool finite_L =  // l_e < +inf, from its exponent bits
-        (__double_as_longlong(p.L) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
-    if (abs_below(xt, p.tol) || (finite_L && abs_below(p.L - xt, p.tol))) p.flags |= 1u;
+    // |x~| < tol, or x~ in (l_e - tol, l_e + tol); a negative x~ within tol
+    // of l_e is within tol of 0 as well
+    const long long b = __double_as_longlong(xt);
+    if (abs_below(xt, p.tol) || (b > p.near_lo && b < p.near_hi)) p.flags |= 1u;
   }
 }
 
