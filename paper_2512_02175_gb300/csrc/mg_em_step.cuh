@@ -130,9 +130,11 @@ __device__ __forceinline__ double u01_f64(uint32_t w) {
 //   r = ph - 1 exact, |r| <= 2^-7;
 //   log1p(r + pl) = r + r^2 q(r) + pl (1 - r), q by the series of log1p to
 //   r^8 (the next term is below 2^-56 of r);
-//   -k ln 2 and -ln c as pairs of binary64 numbers (tables written by
-//   gen_log_table.py), their sum and the sum with r kept exactly (Dekker's
-//   fast two-sum: |k ln 2| >= |ln c| >= |r| wherever the larger is nonzero).
+//   -k ln 2 - ln c as one pair of binary64 numbers per (k, j) (a table
+//   written by gen_log_table.py, one 16-byte load), its sum with r kept
+//   exactly (Dekker's fast two-sum: |k ln 2 + ln c| >= |r| wherever the
+//   former is nonzero, since |r| <= 1 / (2 (64 + j)) while k ln 2 + ln c =
+//   ln(2^k 64 / (64 + j)) is zero or at least ln(128 / 127) in magnitude).
 // Near u = 1 (k = 0, c = 1) the result is r + r^2 q alone: full relative
 // accuracy.
 __device__ __forceinline__ double ln_u01(uint32_t w) {
@@ -159,10 +161,9 @@ __device__ __forceinline__ double ln_u01(uint32_t w) {
   q = fma(q, r, -0.25);
   q = fma(q, r, 1.0 / 3.0);
   q = fma(q, r, -0.5);
-  const double eh = __ldg(&kLn2Hi[k]), th = __ldg(&kLogTHi[j]);
-  const double s = eh + th, es = th - (s - eh);
-  const double t1 = s + r, e1 = r - (t1 - s);
-  const double small = (((__ldg(&kLn2Lo[k]) + __ldg(&kLogTLo[j])) + es) + e1) + fma(-pl, r, pl);
+  const double2 v = __ldg(&kLogKJ[64 * k + j]);  // -k ln 2 - ln c = v.x + v.y
+  const double t1 = v.x + r, e1 = r - (t1 - v.x);
+  const double small = (v.y + e1) + fma(-pl, r, pl);
   return t1 + fma(r * r, q, small);
 }
 

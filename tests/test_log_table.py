@@ -2,8 +2,8 @@
 tables in mg_log_table.h written by gen_log_table.py), checked on the CPU:
 
 * every table entry against a 40-digit logarithm: c_j is the binary64
-  nearest 64 / (64 + j), and hi + lo equals -ln(c_j) (resp. -k ln 2) to
-  within 2^-100 relative;
+  nearest 64 / (64 + j), and hi + lo equals -k ln 2 - ln(c_j) to within
+  2^-100 relative (hi the nearest binary64);
 * the kernel's steps, emulated in binary64 (fused multiply-adds exactly
   rounded through fractions), give the correctly rounded ln u on the ends of
   the range, on both sides of the fold at f = 2 - 2^-7 and of every table
@@ -24,19 +24,20 @@ mpmath = pytest.importorskip("mpmath")
 
 HEADER = os.path.join(os.path.dirname(__file__), "..", "paper_2512_02175_gb300", "csrc",
                       "mg_log_table.h")
+K, J = 34, 64
 
 
 def _tables():
     src = open(HEADER).read()
+    body = re.search(r"const double kLogC\[\d+\] = \{(.*?)\};", src, re.S).group(1)
+    c = [float.fromhex(v.strip()) for v in body.split(",") if v.strip()]
+    body = re.search(r"const double2 kLogKJ\[\d+\] = \{(.*?)\};\n", src, re.S).group(1)
+    kj = [(float.fromhex(h), float.fromhex(l))
+          for h, l in re.findall(r"\{\s*([-0-9a-fx.p+]+)\s*,\s*([-0-9a-fx.p+]+)\s*\}", body)]
+    return c, kj
 
-    def tab(name):
-        body = re.search(r"const double " + name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
-        return [float.fromhex(v.strip()) for v in body.split(",") if v.strip()]
 
-    return tuple(tab(n) for n in ("kLogC", "kLogTHi", "kLogTLo", "kLn2Hi", "kLn2Lo"))
-
-
-C, TH, TL, EH, EL = _tables()
+C, KJ = _tables()
 
 
 def _fma(a, b, c):
@@ -66,28 +67,25 @@ def ln_u01(w):
     q = _fma(r, -0.125, 1.0 / 7.0)
     for coef in (-1.0 / 6.0, 0.2, -0.25, 1.0 / 3.0, -0.5):
         q = _fma(q, r, coef)
-    eh, th = EH[k], TH[j]
-    s = eh + th
-    es = th - (s - eh)
-    t1 = s + r
-    e1 = r - (t1 - s)
-    small = (((EL[k] + TL[j]) + es) + e1) + _fma(-pl, r, pl)
+    vh, vl = KJ[J * k + j]
+    t1 = vh + r
+    e1 = r - (t1 - vh)
+    small = (vl + e1) + _fma(-pl, r, pl)
     return t1 + _fma(r * r, q, small)
 
 
 def test_table_entries():
     mpmath.mp.dps = 40
-    assert len(C) == 65 and len(EH) == 34
+    assert len(C) == 65 and len(KJ) == K * J
     for j in range(65):
         assert C[j] == float(mpmath.mpf(64) / (64 + j))
-        exact = -mpmath.log(mpmath.mpf(C[j]))
-        got = mpmath.mpf(TH[j]) + mpmath.mpf(TL[j])
-        assert abs(got - exact) <= abs(exact) * mpmath.mpf(2) ** -100
-        assert TH[j] == float(exact)
-    assert C[0] == 1.0 and TH[0] == 0.0 and TL[0] == 0.0
-    for k in range(34):
-        exact = -k * mpmath.log(2)
-        assert abs(mpmath.mpf(EH[k]) + mpmath.mpf(EL[k]) - exact) <= (k + 1) * mpmath.mpf(2) ** -100
+    assert C[0] == 1.0 and KJ[0] == (0.0, 0.0)
+    for k in range(K):
+        for j in range(J):
+            exact = -k * mpmath.log(2) - mpmath.log(mpmath.mpf(C[j]))
+            hi, lo = KJ[J * k + j]
+            assert hi == float(exact)
+            assert abs(mpmath.mpf(hi) + mpmath.mpf(lo) - exact) <= abs(exact) * mpmath.mpf(2) ** -100
 
 
 def _words():
