@@ -115,3 +115,22 @@ def test_correctly_rounded():
         if err > 0.5 + 1e-9:
             bad.append((w, float(err)))
     assert not bad, bad[:5]
+
+
+def test_header_is_the_generators_output():
+    """mg_log_table.h is exactly what gen_log_table.py writes (no hand edits)."""
+    import contextlib
+    import importlib.util
+    import io
+    gen = os.path.join(os.path.dirname(HEADER), "gen_log_table.py")
+    spec = importlib.util.spec_from_file_location("gen_log_table", gen)
+    mod = importlib.util.module_from_spec(spec)
+    dps = mpmath.mp.dps
+    spec.loader.exec_module(mod)
+    buf = io.StringIO()
+    try:
+        with contextlib.redirect_stdout(buf):
+            mod.main()
+    finally:
+        mpmath.mp.dps = dps
+    assert buf.getvalue() == open(HEADER).read()
